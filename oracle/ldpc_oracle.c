@@ -1,0 +1,473 @@
+/*
+ * ldpc_oracle.c -- TEST INFRASTRUCTURE ONLY (see ldpc_oracle.h).
+ *
+ * Every function follows the paper's equations in their order and notation,
+ * one frame at a time, with no blocking, fusion or reordering.  Check messages
+ * are computed literally as a product of signs and a minimum over N(m)\n
+ * (quadratic in the check degree) rather than through min1/min2 bookkeeping.
+ * Frames are independent problems; they are split across POSIX threads.
+ */
+#include "ldpc_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+/* ------------------------------------------------------------------ common */
+
+static int sgn_i(int64_t v) { return (v > 0) - (v < 0); }
+static int sgn_d(double v) { return (v > 0.0) - (v < 0.0); }
+
+/* Section III: magnitude modification of a check message.  Normalized:
+   L <= lambda_k L (magnitude floored in integers).  Offset: L <= max(L - beta, 0),
+   read as acting on |L|. */
+static int64_t modify_i(const orc_iparams *p, int64_t mag) {
+  if (p->rule == ORC_OFFSET) return mag > p->offset ? mag - p->offset : 0;
+  if (p->rule == ORC_NORMALIZED) return (mag * p->norm_num) >> p->norm_shift;
+  return mag;
+}
+
+static double modify_d(const orc_dparams *p, int32_t k, int32_t m, int32_t n_checks, double mag) {
+  if (p->rule == ORC_OFFSET) {
+    double beta = p->beta_tab ? p->beta_tab[(size_t)(k - 1) * n_checks + m] : p->offset;
+    return mag > beta ? mag - beta : 0.0;
+  }
+  if (p->rule == ORC_NORMALIZED) return p->lambda * mag;
+  return mag;
+}
+
+static int64_t sat_i(const orc_iparams *p, int64_t mag) {
+  return (p->msg_sat > 0 && mag > p->msg_sat) ? p->msg_sat : mag;
+}
+
+/* Decoding step (Section III): x_n = 0 if Z_n > 0, else 1.  Returns 1 when
+   H x^T = 0. */
+static int decide_and_check(const orc_code *c, const int64_t *Zi, const double *Zd,
+                            uint8_t *x) {
+  for (int32_t n = 0; n < c->n_vars; ++n) x[n] = Zi ? (Zi[n] > 0 ? 0 : 1) : (Zd[n] > 0.0 ? 0 : 1);
+  for (int32_t m = 0; m < c->n_checks; ++m) {
+    int par = 0;
+    for (int32_t e = c->row_ptr[m]; e < c->row_ptr[m + 1]; ++e) par ^= x[c->col_idx[e]];
+    if (par) return 0;
+  }
+  return 1;
+}
+
+/* Variable->check adjacency M(n) (CSC with edge ids), needed by the vertical
+   scan of the two-scan algorithm only. */
+typedef struct {
+  int32_t *col_ptr; /* [N+1] */
+  int32_t *edge;    /* [E] edge ids grouped by variable */
+} orc_csc;
+
+static int build_csc(const orc_code *c, orc_csc *t) {
+  int32_t E = c->row_ptr[c->n_checks];
+  t->col_ptr = (int32_t *)calloc((size_t)c->n_vars + 1, sizeof(int32_t));
+  t->edge = (int32_t *)malloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
+  int32_t *fill = (int32_t *)calloc((size_t)c->n_vars + 1, sizeof(int32_t));
+  if (!t->col_ptr || !t->edge || !fill) { free(fill); return -1; }
+  for (int32_t e = 0; e < E; ++e) t->col_ptr[c->col_idx[e] + 1]++;
+  for (int32_t n = 0; n < c->n_vars; ++n) t->col_ptr[n + 1] += t->col_ptr[n];
+  for (int32_t e = 0; e < E; ++e) {
+    int32_t n = c->col_idx[e];
+    t->edge[t->col_ptr[n] + fill[n]++] = e;
+  }
+  free(fill);
+  return 0;
+}
+
+static void free_csc(orc_csc *t) { free(t->col_ptr); free(t->edge); }
+
+/* Eq. (1) / Eq. (3) for one position j of a check with inputs in[0..d-1]:
+   product of sgn over the other positions times the minimum over the other
+   positions of the (saturated) magnitude. */
+static int64_t check_rule_i(const orc_iparams *p, const int64_t *in, int32_t d, int32_t j) {
+  int s = 1;
+  int64_t mn = -1;
+  for (int32_t t = 0; t < d; ++t) {
+    if (t == j) continue;
+    s *= sgn_i(in[t]);
+    int64_t a = sat_i(p, in[t] < 0 ? -in[t] : in[t]);
+    if (mn < 0 || a < mn) mn = a;
+  }
+  return (int64_t)s * mn;
+}
+
+static double check_rule_d(const double *in, int32_t d, int32_t j) {
+  int s = 1;
+  double mn = INFINITY;
+  for (int32_t t = 0; t < d; ++t) {
+    if (t == j) continue;
+    s *= sgn_d(in[t]);
+    double a = fabs(in[t]);
+    if (a < mn) mn = a;
+  }
+  return (double)s * mn;
+}
+
+/* ------------------------------------------------------- integer, one frame */
+
+typedef struct {
+  int64_t *Z, *Zprev, *L, *Zmn, *u, *Lraw;
+  int64_t *A, *B;
+  int32_t *nt;
+  int8_t *s;
+  uint8_t *x;
+} iscratch;
+
+static void decode_frame_int(const orc_code *c, const orc_csc *t, const orc_iparams *p,
+                             int32_t form, const int32_t *q0, iscratch *w, uint8_t *bits,
+                             int32_t *iters, uint8_t *ok, int32_t *z_out, int32_t *l_out,
+                             int32_t *state_out) {
+  const int32_t N = c->n_vars, M = c->n_checks, E = c->row_ptr[M];
+  const int32_t *rp = c->row_ptr, *ci = c->col_idx;
+  int64_t *Z = w->Z, *Zprev = w->Zprev, *L = w->L;
+
+  /* k = 0: Z^(0)_n = q0_n, L^(0) = 0 (Section IV initialization; Section III
+     initialization Z^(0)_mn = Z^(0)_n). */
+  for (int32_t n = 0; n < N; ++n) Z[n] = q0[n];
+  for (int32_t e = 0; e < E; ++e) { L[e] = 0; w->Zmn[e] = q0[ci[e]]; w->s[e] = 0; }
+  for (int32_t m = 0; m < M; ++m) { w->A[m] = 0; w->B[m] = 0; w->nt[m] = 0; }
+
+  int32_t k = 0;
+  int sat = decide_and_check(c, Z, NULL, w->x);
+  if (!(p->early_stop && sat)) {
+    for (k = 1; k <= p->max_iter; ++k) {
+      memcpy(Zprev, Z, sizeof(int64_t) * (size_t)N);
+      if (form == ORC_TWO_SCAN) {
+        /* Horizontal scan, Eq. (1), then the normalized/offset modification. */
+        for (int32_t m = 0; m < M; ++m) {
+          int32_t d = rp[m + 1] - rp[m];
+          for (int32_t j = 0; j < d; ++j) w->u[j] = w->Zmn[rp[m] + j];
+          for (int32_t j = 0; j < d; ++j) {
+            int64_t l = check_rule_i(p, w->u, d, j);
+            L[rp[m] + j] = sgn_i(l) * modify_i(p, l < 0 ? -l : l);
+          }
+        }
+        /* Vertical scan, Eq. (2): Z_mn = Z0_n + sum over M(n)\m of L_m'n. */
+        for (int32_t n = 0; n < N; ++n) {
+          for (int32_t a = t->col_ptr[n]; a < t->col_ptr[n + 1]; ++a) {
+            int64_t acc = q0[n];
+            for (int32_t b = t->col_ptr[n]; b < t->col_ptr[n + 1]; ++b)
+              if (b != a) acc += L[t->edge[b]];
+            w->Zmn[t->edge[a]] = acc;
+          }
+          /* Decoding step: Z_n = Z0_n + sum over M(n) of L_mn. */
+          int64_t post = q0[n];
+          for (int32_t b = t->col_ptr[n]; b < t->col_ptr[n + 1]; ++b) post += L[t->edge[b]];
+          Z[n] = post;
+        }
+      } else if (form == ORC_SS_FIXED) {
+        /* Eq. (3): Z^(k)_n = Z^(0)_n; per check, L^(k)_mn from
+           Z^(k-1)_n' - L^(k-1)_mn'; then Z^(k)_n += L^(k)_mn. */
+        for (int32_t n = 0; n < N; ++n) Z[n] = q0[n];
+        for (int32_t m = 0; m < M; ++m) {
+          int32_t d = rp[m + 1] - rp[m];
+          for (int32_t j = 0; j < d; ++j) w->u[j] = Zprev[ci[rp[m] + j]] - L[rp[m] + j];
+          for (int32_t j = 0; j < d; ++j) {
+            int64_t l = check_rule_i(p, w->u, d, j);
+            w->Lraw[j] = sgn_i(l) * modify_i(p, l < 0 ? -l : l);
+          }
+          for (int32_t j = 0; j < d; ++j) {
+            L[rp[m] + j] = w->Lraw[j];
+            Z[ci[rp[m] + j]] += w->Lraw[j];
+          }
+        }
+      } else {
+        /* Section V: rebuild L^(k-1)_mn = s f(A, B, n, n~), apply Eq. (3),
+           then store A = g(min |L|), B = g(max |L|), n~ = argmax |L|, s = sgn L
+           (Eqs. (4), (5) with the normalized/offset change), and accumulate
+           the stored message into Z. */
+        for (int32_t n = 0; n < N; ++n) Z[n] = q0[n];
+        for (int32_t m = 0; m < M; ++m) {
+          int32_t d = rp[m + 1] - rp[m];
+          for (int32_t j = 0; j < d; ++j) {
+            int64_t f = (j == w->nt[m]) ? w->B[m] : w->A[m];
+            int64_t lold = (int64_t)w->s[rp[m] + j] * f;
+            w->u[j] = Zprev[ci[rp[m] + j]] - lold;
+          }
+          for (int32_t j = 0; j < d; ++j) w->Lraw[j] = check_rule_i(p, w->u, d, j);
+          int64_t amin = -1, amax = -1;
+          int32_t arg = 0;
+          for (int32_t j = 0; j < d; ++j) {
+            int64_t a = w->Lraw[j] < 0 ? -w->Lraw[j] : w->Lraw[j];
+            if (amin < 0 || a < amin) amin = a;
+            if (a > amax) { amax = a; arg = j; }
+          }
+          w->A[m] = modify_i(p, amin);
+          w->B[m] = modify_i(p, amax);
+          w->nt[m] = arg;
+          for (int32_t j = 0; j < d; ++j) {
+            w->s[rp[m] + j] = (int8_t)sgn_i(w->Lraw[j]);
+            int64_t f = (j == arg) ? w->B[m] : w->A[m];
+            int64_t lnew = (int64_t)w->s[rp[m] + j] * f;
+            L[rp[m] + j] = lnew;
+            Z[ci[rp[m] + j]] += lnew;
+          }
+        }
+      }
+      sat = decide_and_check(c, Z, NULL, w->x);
+      if (p->early_stop && sat) break;
+    }
+    if (k > p->max_iter) k = p->max_iter;
+  }
+  *iters = k;
+  *ok = (uint8_t)sat;
+  for (int32_t n = 0; n < N; ++n) { bits[n] = w->x[n]; z_out[n] = (int32_t)Z[n]; }
+  if (l_out)
+    for (int32_t e = 0; e < E; ++e) l_out[e] = (int32_t)L[e];
+  if (state_out && form == ORC_SS_1BIT) {
+    for (int32_t m = 0; m < M; ++m) {
+      int32_t sw = 0;
+      for (int32_t j = 0; j < rp[m + 1] - rp[m]; ++j)
+        if (w->s[rp[m] + j] < 0) sw |= (int32_t)(1u << j);
+      state_out[4 * m + 0] = (int32_t)w->A[m];
+      state_out[4 * m + 1] = (int32_t)w->B[m];
+      state_out[4 * m + 2] = w->nt[m];
+      state_out[4 * m + 3] = sw;
+    }
+  }
+}
+
+/* -------------------------------------------------- double, one frame */
+
+typedef struct {
+  double *Z, *Zprev, *L, *Zmn, *u, *Lraw, *A, *B;
+  int32_t *nt;
+  int8_t *s;
+  uint8_t *x;
+} dscratch;
+
+static void decode_frame_f64(const orc_code *c, const orc_csc *t, const orc_dparams *p,
+                             int32_t form, const double *q0, dscratch *w, uint8_t *bits,
+                             int32_t *iters, uint8_t *ok, double *z_out, double *l_out) {
+  const int32_t N = c->n_vars, M = c->n_checks, E = c->row_ptr[M];
+  const int32_t *rp = c->row_ptr, *ci = c->col_idx;
+  double *Z = w->Z, *Zprev = w->Zprev, *L = w->L;
+
+  for (int32_t n = 0; n < N; ++n) Z[n] = q0[n];
+  for (int32_t e = 0; e < E; ++e) { L[e] = 0.0; w->Zmn[e] = q0[ci[e]]; w->s[e] = 0; }
+  for (int32_t m = 0; m < M; ++m) { w->A[m] = 0.0; w->B[m] = 0.0; w->nt[m] = 0; }
+
+  int32_t k = 0;
+  int sat = decide_and_check(c, NULL, Z, w->x);
+  if (!(p->early_stop && sat)) {
+    for (k = 1; k <= p->max_iter; ++k) {
+      memcpy(Zprev, Z, sizeof(double) * (size_t)N);
+      if (form == ORC_TWO_SCAN) {
+        for (int32_t m = 0; m < M; ++m) {
+          int32_t d = rp[m + 1] - rp[m];
+          for (int32_t j = 0; j < d; ++j) w->u[j] = w->Zmn[rp[m] + j];
+          for (int32_t j = 0; j < d; ++j) {
+            double l = check_rule_d(w->u, d, j);
+            L[rp[m] + j] = sgn_d(l) * modify_d(p, k, m, M, fabs(l));
+          }
+        }
+        for (int32_t n = 0; n < N; ++n) {
+          for (int32_t a = t->col_ptr[n]; a < t->col_ptr[n + 1]; ++a) {
+            double acc = q0[n];
+            for (int32_t b = t->col_ptr[n]; b < t->col_ptr[n + 1]; ++b)
+              if (b != a) acc += L[t->edge[b]];
+            w->Zmn[t->edge[a]] = acc;
+          }
+          double post = q0[n];
+          for (int32_t b = t->col_ptr[n]; b < t->col_ptr[n + 1]; ++b) post += L[t->edge[b]];
+          Z[n] = post;
+        }
+      } else if (form == ORC_SS_FIXED) {
+        for (int32_t n = 0; n < N; ++n) Z[n] = q0[n];
+        for (int32_t m = 0; m < M; ++m) {
+          int32_t d = rp[m + 1] - rp[m];
+          for (int32_t j = 0; j < d; ++j) w->u[j] = Zprev[ci[rp[m] + j]] - L[rp[m] + j];
+          for (int32_t j = 0; j < d; ++j) {
+            double l = check_rule_d(w->u, d, j);
+            w->Lraw[j] = sgn_d(l) * modify_d(p, k, m, M, fabs(l));
+          }
+          for (int32_t j = 0; j < d; ++j) {
+            L[rp[m] + j] = w->Lraw[j];
+            Z[ci[rp[m] + j]] += w->Lraw[j];
+          }
+        }
+      } else {
+        for (int32_t n = 0; n < N; ++n) Z[n] = q0[n];
+        for (int32_t m = 0; m < M; ++m) {
+          int32_t d = rp[m + 1] - rp[m];
+          for (int32_t j = 0; j < d; ++j) {
+            double f = (j == w->nt[m]) ? w->B[m] : w->A[m];
+            w->u[j] = Zprev[ci[rp[m] + j]] - (double)w->s[rp[m] + j] * f;
+          }
+          for (int32_t j = 0; j < d; ++j) w->Lraw[j] = check_rule_d(w->u, d, j);
+          double amin = INFINITY, amax = -1.0;
+          int32_t arg = 0;
+          for (int32_t j = 0; j < d; ++j) {
+            double a = fabs(w->Lraw[j]);
+            if (a < amin) amin = a;
+            if (a > amax) { amax = a; arg = j; }
+          }
+          w->A[m] = modify_d(p, k, m, M, amin);
+          w->B[m] = modify_d(p, k, m, M, amax);
+          w->nt[m] = arg;
+          for (int32_t j = 0; j < d; ++j) {
+            w->s[rp[m] + j] = (int8_t)sgn_d(w->Lraw[j]);
+            double f = (j == arg) ? w->B[m] : w->A[m];
+            double lnew = (double)w->s[rp[m] + j] * f;
+            L[rp[m] + j] = lnew;
+            Z[ci[rp[m] + j]] += lnew;
+          }
+        }
+      }
+      sat = decide_and_check(c, NULL, Z, w->x);
+      if (p->early_stop && sat) break;
+    }
+    if (k > p->max_iter) k = p->max_iter;
+  }
+  *iters = k;
+  *ok = (uint8_t)sat;
+  for (int32_t n = 0; n < N; ++n) { bits[n] = w->x[n]; z_out[n] = Z[n]; }
+  if (l_out)
+    for (int32_t e = 0; e < E; ++e) l_out[e] = L[e];
+}
+
+/* ------------------------------------------------------------ threading */
+
+typedef struct {
+  const orc_code *c;
+  const orc_csc *t;
+  int32_t form;
+  int is_int;
+  const orc_iparams *ip;
+  const orc_dparams *dp;
+  const void *q0;
+  int32_t f0, f1;
+  uint8_t *bits;
+  int32_t *iters;
+  uint8_t *ok;
+  void *z_out, *l_out;
+  int32_t *state_out;
+  int err;
+} job;
+
+static int32_t max_row_degree(const orc_code *c) {
+  int32_t dmax = 0;
+  for (int32_t m = 0; m < c->n_checks; ++m)
+    if (c->row_ptr[m + 1] - c->row_ptr[m] > dmax) dmax = c->row_ptr[m + 1] - c->row_ptr[m];
+  return dmax;
+}
+
+static void *run_job(void *arg) {
+  job *jb = (job *)arg;
+  const orc_code *c = jb->c;
+  size_t N = (size_t)c->n_vars, M = (size_t)c->n_checks, E = (size_t)c->row_ptr[c->n_checks];
+  size_t D = (size_t)max_row_degree(c) + 1;
+  if (jb->is_int) {
+    iscratch w;
+    w.Z = malloc(sizeof(int64_t) * (N + 1)); w.Zprev = malloc(sizeof(int64_t) * (N + 1));
+    w.L = malloc(sizeof(int64_t) * (E + 1)); w.Zmn = malloc(sizeof(int64_t) * (E + 1));
+    w.u = malloc(sizeof(int64_t) * D); w.Lraw = malloc(sizeof(int64_t) * D);
+    w.A = malloc(sizeof(int64_t) * (M + 1)); w.B = malloc(sizeof(int64_t) * (M + 1));
+    w.nt = malloc(sizeof(int32_t) * (M + 1)); w.s = malloc(E + 1); w.x = malloc(N + 1);
+    if (!w.Z || !w.Zprev || !w.L || !w.Zmn || !w.u || !w.Lraw || !w.A || !w.B || !w.nt || !w.s || !w.x) {
+      jb->err = -1;
+    } else {
+      const int32_t *q0 = (const int32_t *)jb->q0;
+      for (int32_t f = jb->f0; f < jb->f1; ++f)
+        decode_frame_int(c, jb->t, jb->ip, jb->form, q0 + (size_t)f * N, &w, jb->bits + (size_t)f * N,
+                         jb->iters + f, jb->ok + f, (int32_t *)jb->z_out + (size_t)f * N,
+                         jb->l_out ? (int32_t *)jb->l_out + (size_t)f * E : NULL,
+                         jb->state_out ? jb->state_out + (size_t)f * M * 4 : NULL);
+    }
+    free(w.Z); free(w.Zprev); free(w.L); free(w.Zmn); free(w.u); free(w.Lraw);
+    free(w.A); free(w.B); free(w.nt); free(w.s); free(w.x);
+  } else {
+    dscratch w;
+    w.Z = malloc(sizeof(double) * (N + 1)); w.Zprev = malloc(sizeof(double) * (N + 1));
+    w.L = malloc(sizeof(double) * (E + 1)); w.Zmn = malloc(sizeof(double) * (E + 1));
+    w.u = malloc(sizeof(double) * D); w.Lraw = malloc(sizeof(double) * D);
+    w.A = malloc(sizeof(double) * (M + 1)); w.B = malloc(sizeof(double) * (M + 1));
+    w.nt = malloc(sizeof(int32_t) * (M + 1)); w.s = malloc(E + 1); w.x = malloc(N + 1);
+    if (!w.Z || !w.Zprev || !w.L || !w.Zmn || !w.u || !w.Lraw || !w.A || !w.B || !w.nt || !w.s || !w.x) {
+      jb->err = -1;
+    } else {
+      const double *q0 = (const double *)jb->q0;
+      for (int32_t f = jb->f0; f < jb->f1; ++f)
+        decode_frame_f64(c, jb->t, jb->dp, jb->form, q0 + (size_t)f * N, &w, jb->bits + (size_t)f * N,
+                         jb->iters + f, jb->ok + f, (double *)jb->z_out + (size_t)f * N,
+                         jb->l_out ? (double *)jb->l_out + (size_t)f * E : NULL);
+    }
+    free(w.Z); free(w.Zprev); free(w.L); free(w.Zmn); free(w.u); free(w.Lraw);
+    free(w.A); free(w.B); free(w.nt); free(w.s); free(w.x);
+  }
+  return NULL;
+}
+
+int32_t orc_default_threads(void) {
+  long n = sysconf(_SC_NPROCESSORS_ONLN);
+  return n > 0 ? (int32_t)n : 1;
+}
+
+static int validate(const orc_code *c, int32_t form) {
+  if (!c || c->n_vars < 0 || c->n_checks < 0 || !c->row_ptr) return -1;
+  if (form < ORC_TWO_SCAN || form > ORC_SS_1BIT) return -1;
+  if (c->row_ptr[0] != 0) return -1;
+  for (int32_t m = 0; m < c->n_checks; ++m) {
+    int32_t d = c->row_ptr[m + 1] - c->row_ptr[m];
+    if (d < 2 || d > 32) return -1; /* empty N(m)\n is undefined in Eq. (1) */
+    for (int32_t e = c->row_ptr[m]; e < c->row_ptr[m + 1]; ++e)
+      if (c->col_idx[e] < 0 || c->col_idx[e] >= c->n_vars) return -1;
+  }
+  return 0;
+}
+
+static int run_all(job *proto, int32_t n_frames, int32_t n_threads) {
+  if (n_threads <= 0) n_threads = orc_default_threads();
+  if (n_threads > n_frames) n_threads = n_frames > 0 ? n_frames : 1;
+  orc_csc t = {0, 0};
+  if (build_csc(proto->c, &t)) { free_csc(&t); return -1; }
+  proto->t = &t;
+  job *jobs = (job *)calloc((size_t)n_threads, sizeof(job));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  int err = (!jobs || !th) ? -1 : 0;
+  int32_t started = 0;
+  for (int32_t i = 0; i < n_threads && !err; ++i) {
+    jobs[i] = *proto;
+    jobs[i].f0 = (int32_t)((int64_t)n_frames * i / n_threads);
+    jobs[i].f1 = (int32_t)((int64_t)n_frames * (i + 1) / n_threads);
+    if (pthread_create(&th[i], NULL, run_job, &jobs[i])) err = -1;
+    else started++;
+  }
+  for (int32_t i = 0; i < started; ++i) {
+    pthread_join(th[i], NULL);
+    if (jobs[i].err) err = -1;
+  }
+  free(jobs); free(th); free_csc(&t);
+  return err;
+}
+
+int orc_decode_int(const orc_code *code, const orc_iparams *p, int32_t form, const int32_t *q0,
+                   int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok, int32_t *z_out,
+                   int32_t *l_out, int32_t *state_out, int32_t n_threads) {
+  if (validate(code, form) || !p || p->max_iter < 0 || n_frames < 0) return -1;
+  if (n_frames == 0) return 0;
+  if (!q0 || !bits || !iters || !ok || !z_out) return -1;
+  job proto;
+  memset(&proto, 0, sizeof proto);
+  proto.c = code; proto.form = form; proto.is_int = 1; proto.ip = p; proto.q0 = q0;
+  proto.bits = bits; proto.iters = iters; proto.ok = ok; proto.z_out = z_out;
+  proto.l_out = l_out; proto.state_out = state_out;
+  return run_all(&proto, n_frames, n_threads);
+}
+
+int orc_decode_f64(const orc_code *code, const orc_dparams *p, int32_t form, const double *q0,
+                   int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok, double *z_out,
+                   double *l_out, int32_t n_threads) {
+  if (validate(code, form) || !p || p->max_iter < 0 || n_frames < 0) return -1;
+  if (n_frames == 0) return 0;
+  if (!q0 || !bits || !iters || !ok || !z_out) return -1;
+  job proto;
+  memset(&proto, 0, sizeof proto);
+  proto.c = code; proto.form = form; proto.is_int = 0; proto.dp = p; proto.q0 = q0;
+  proto.bits = bits; proto.iters = iters; proto.ok = ok; proto.z_out = z_out; proto.l_out = l_out;
+  return run_all(&proto, n_frames, n_threads);
+}

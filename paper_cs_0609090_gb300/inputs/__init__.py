@@ -1,0 +1,14 @@
+"""Seeded synthetic inputs: codes (H in CSR form), codewords and channel LLRs.
+
+Shared by the oracle tests and the CUDA path; contains none of the decoder's
+arithmetic.  Importing this subpackage never loads the CUDA library.
+"""
+from .codes import (Code, from_rows, hamming74, regular_code, qc_code, staircase_code,
+                    tree_code, permuted)
+from .encode import Encoder, rref_gf2, syndrome
+from .channel import awgn_llr, quantize, noiseless, sigma2
+from .workloads import WORKLOADS, make_workload, Workload
+
+__all__ = ["Code", "from_rows", "hamming74", "regular_code", "qc_code", "staircase_code",
+           "tree_code", "permuted", "Encoder", "rref_gf2", "syndrome", "awgn_llr",
+           "quantize", "noiseless", "sigma2", "WORKLOADS", "make_workload", "Workload"]
