@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Decoded-information throughput of the single-scan min-sum decoder on GB300.
+
+One step = one ldpc_decode_batch call over the whole workload batch with early
+stop off (every frame runs the fixed iteration count), LLRs already resident
+in HBM.  ``value`` = decoded information bits (F * K per step) per second,
+whole job over all ranks; ``e2e`` is the same through the C ABI with the LLRs
+copied from pinned host memory and the decisions/iterations/flags copied back
+inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload qc_n7493]
+                  [--form ss_1bit|ss_fixed] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (the only reference this method has)
+on a bounded sample of the same workload and prints the same JSON line.
+Multi-GPU (torchrun): every rank decodes its own batch (frames are independent;
+weak scaling, no collective on the data path); time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_cs_0609090_gb300 import inputs as I  # noqa: E402
+
+METRIC = "decoded info Gbit/s at fixed iters, single-scan vs two-scan; FER @ stated Eb/N0"
+UNIT = "Gbit/s"
+
+
+def algorithmic_bytes(code, form: str, iters: int, frames: int) -> dict:
+    """Streaming-model bytes of one decode: per frame-iteration 2 b_z N + 2 S_L
+    (read and write of the posterior and of the message state) plus per frame
+    the int8 LLRs in, packed decisions out and 5 bytes of iteration count/flag."""
+    N, M, E = code.n_vars, code.n_checks, code.n_edges
+    dmax = int(code.row_degrees().max())
+    b_z = 2
+    if form == "ss_1bit":
+        s_l = ((dmax + 7) // 8 + 3) * M
+    elif form == "ss_fixed":
+        s_l = E
+    else:  # two-scan: Z_mn and L_mn cells read and written, plus q0 and decisions
+        s_l = None
+    if s_l is None:
+        b_it = 4 * E + N + N // 8
+    else:
+        b_it = 2 * b_z * N + 2 * s_l
+    b_io = N + (N + 7) // 8 + 5
+    return dict(per_frame_iter=b_it, per_frame_io=b_io, per_launch=frames * (iters * b_it + b_io))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_cs_0609090_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_cs_0609090_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str, form: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; otherwise None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(f"{kernel}/{workload}/{form}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_oracle_sample(w, form: str, budget_s: float, max_frames: int):
+    """Times the CPU oracle on successive chunks of the workload's frames until
+    ``budget_s`` seconds of wall time or ``max_frames`` frames."""
+    import oracle
+    p = w.params
+    chunk = max(oracle.default_threads() * 2, 8)
+    done, t_total = 0, 0.0
+    while done < max_frames and t_total < budget_s:
+        q = w.q0[done % w.n_frames:][:chunk]
+        t0 = time.perf_counter()
+        oracle.decode_int(w.code, q, form=form, rule=p["rule"], offset=p.get("offset", 0),
+                          norm_num=p.get("norm_num", 3), norm_shift=p.get("norm_shift", 2),
+                          msg_sat=p["msg_sat"], max_iter=p["max_iter"], early_stop=0)
+        t_total += time.perf_counter() - t0
+        done += q.shape[0]
+    gbps = done * w.K / t_total / 1e9
+    return dict(value=gbps, unit=UNIT, cores=oracle.default_threads(), kind="oracle",
+                sample=f"{done} of {w.n_frames} frames of {w.name}, {p['max_iter']} iterations, "
+                       f"early stop off, {form}, {t_total:.1f} s"), t_total / done
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    w = I.make_workload(args.workload)
+    w.params["early_stop"] = 0
+    budget = float(os.environ.get("BENCH_REF_BUDGET_S", "8"))
+    per_step = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        info, sec_per_frame = cpu_oracle_sample(w, args.form, budget_s=budget if s >= args.warmup else 1.0,
+                                                max_frames=w.n_frames)
+        if s >= args.warmup:
+            per_step.append(info["value"])
+    val = float(np.median(per_step))
+    info["value"] = val
+    ms = w.n_frames * w.K / (val * 1e9) * 1e3
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": w.name, "form": args.form, "n_frames": w.n_frames,
+                       "iters": w.params["max_iter"], "N": w.code.n_vars, "K": w.K},
+            "impl": "reference", "cpu_baseline": info,
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="qc_n7493")
+    ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_cs_0609090_gb300 import ldpc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = I.make_workload(args.workload, frame_seed=1 + rank)
+    w.params["early_stop"] = 0
+    F, N, K = w.n_frames, w.code.n_vars, w.K
+    code = ldpc.Code.from_inputs(w.code, device=local)
+    params = ldpc.make_params(form=args.form, **w.params)
+    llr = torch.from_numpy(w.q0).to(dev)
+    bits = torch.empty((F, (N + 7) // 8), dtype=torch.uint8, device=dev)
+    iters = torch.empty(F, dtype=torch.int32, device=dev)
+    ok = torch.empty(F, dtype=torch.uint8, device=dev)
+    ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
+    ws = torch.empty(max(ws_bytes, 1) + 256, dtype=torch.uint8, device=dev)
+    ws_ptr = (ws.data_ptr() + 255) & ~255
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
+
+    class _WS:  # aligned workspace pointer for the binding
+        def data_ptr(self):
+            return ws_ptr
+
+    def step():
+        ldpc.ldpc_decode_batch(code.handle, params, llr, F, bits, iters, ok, None,
+                               _WS() if ws_bytes else None, ws_bytes, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    # sanity: all frames ran the fixed iteration count
+    assert int(iters.min()) == w.params["max_iter"] and int(iters.max()) == w.params["max_iter"]
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)  # evict L2 between timed steps (outside the event pair)
+            evs[s][0].record(stream)
+            step()
+            evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    dev_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(np.sum(dev_ms))
+
+    # end to end through the C ABI: pinned host LLRs in, decisions/iters/flags out
+    h_llr = torch.from_numpy(w.q0).pin_memory()
+    h_bits = torch.empty_like(bits, device="cpu").pin_memory()
+    h_iters = torch.empty_like(iters, device="cpu").pin_memory()
+    h_ok = torch.empty_like(ok, device="cpu").pin_memory()
+    e2e_evs = []
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            llr.copy_(h_llr, non_blocking=True)
+            step()
+            h_bits.copy_(bits, non_blocking=True)
+            h_iters.copy_(iters, non_blocking=True)
+            h_ok.copy_(ok, non_blocking=True)
+            b.record(stream)
+            e2e_evs.append((a, b))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    e2e_ms = float(np.sum([a.elapsed_time(b) for a, b in e2e_evs]))
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+        dist.barrier()
+    if rank != 0:
+        return 0
+
+    ms_step = total_ms / args.steps
+    value = world * F * K / (ms_step * 1e-3) / 1e9
+    e2e_val = world * F * K / (e2e_ms / args.steps * 1e-3) / 1e9
+    ab = algorithmic_bytes(w.code, args.form, w.params["max_iter"], F)
+    peaks = measured_peaks()
+    achieved = ab["per_launch"] / (ms_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic("onchip_int8_kernel",
+                                                                                  w.name, args.form),
+                "peak_source": peaks["source"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": ab["per_launch"],
+                "bytes_per_frame_iter": ab["per_frame_iter"],
+                "kernel": "onchip_int8_kernel", "kernel_ms": ms_step}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": w.name, "form": args.form, "n_frames": F, "iters": w.params["max_iter"],
+                       "N": N, "M": w.code.n_checks, "E": w.code.n_edges, "K": K,
+                       "ebn0_db": w.ebn0_db, "rule": w.params["rule"], "early_stop": 0,
+                       "l2": "flushed between timed steps (256 MB write)", "frames_per_rank": F},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(w.q0.nbytes),
+                    "d2h_bytes_per_step": int(bits.numel() + iters.numel() * 4 + ok.numel())},
+            "gpu_launches": args.steps,
+            "roofline": roofline, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        info, _ = cpu_oracle_sample(w, args.form, budget_s=float(os.environ.get("BENCH_CPU_BUDGET_S", "12")),
+                                    max_frames=F)
+        line["cpu_baseline"] = info
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * ldpc_gb300.h -- C ABI of the GB300 (sm_103a) single-scan min-sum LDPC decoder.
+ *
+ * The decoder implements Huang, "Single-Scan Min-Sum Algorithms for Fast
+ * Decoding of LDPC Codes" (ITW 2006):
+ *   - Section III: (normalized/offset) min-sum, check rule Eq. (1), the
+ *     posterior Z_n = Z0_n + sum_m L_mn, the decision x_n = 0 iff Z_n > 0 and
+ *     the stop rule H x^T = 0 or an iteration cap;
+ *   - Section IV, Eq. (3): the single scan, which needs only the
+ *     check->variable adjacency N(m) and keeps one message L_mn per edge
+ *     (LDPC_FORM_SS_FIXED);
+ *   - Section V, Eqs. (4)-(5): the single scan whose persistent state per check
+ *     is (A_m, B_m, n~_m) and one sign bit per edge (LDPC_FORM_SS_1BIT);
+ *   - Section III, Eqs. (1)-(2) literally (horizontal then vertical scan), as a
+ *     comparator (LDPC_FORM_TWO_SCAN).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an ldpc_status; nothing is thrown across the ABI.  On
+ *     an error, ldpc_last_error() returns a message for the calling thread.
+ *   - Pointers documented as "device" must be device memory of the code's
+ *     device (or managed memory); "host" pointers are ordinary host memory.
+ *   - The caller owns every buffer it passes in.  The library owns only the
+ *     device copy of a code (created by ldpc_code_create, released by
+ *     ldpc_code_destroy).
+ *   - Decoding calls are asynchronous on the given stream (a cudaStream_t; NULL
+ *     is the legacy default stream).  Outputs are valid once the stream has
+ *     been synchronised.  Frames are independent; n_frames == 0 is a no-op.
+ *   - Numerics: the int8 path is exact integer arithmetic, bit-identical to the
+ *     literal two-scan / single-scan definitions (the posterior is held exactly,
+ *     never saturated); the float32 path accumulates in float32.
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LDPC_API __attribute__((visibility("default")))
+#else
+#define LDPC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ldpc_status;
+#define LDPC_OK 0
+#define LDPC_ERR_INVALID_ARG 1 /* null pointer, malformed H, bad parameter */
+#define LDPC_ERR_UNSUPPORTED 2 /* valid request this build cannot run (sizes, degrees) */
+#define LDPC_ERR_CUDA 3        /* a CUDA runtime call failed */
+#define LDPC_ERR_OOM 4         /* device allocation failed */
+#define LDPC_ERR_TIMEOUT 5     /* a bounded device-side wait gave up */
+
+/* Opaque device-resident description of a code. */
+typedef struct ldpc_code ldpc_code;
+
+enum { LDPC_DTYPE_INT8 = 0, LDPC_DTYPE_F32 = 1 };
+enum { LDPC_FORM_SS_FIXED = 0, LDPC_FORM_SS_1BIT = 1, LDPC_FORM_TWO_SCAN = 2 };
+enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2 };
+
+/* Decoder settings (Section III: lambda_k, beta_k constant over k; cap).
+ *   dtype      LDPC_DTYPE_INT8: llr is int8, messages are integers saturated to
+ *              msg_sat; LDPC_DTYPE_F32: llr is float32.
+ *   form       which of the three algorithms above runs.
+ *   rule       PLAIN; OFFSET: |L| <- max(|L| - beta, 0); NORMALIZED: |L| <- lambda |L|.
+ *   offset     int8 path: beta in LSBs (>= 0).
+ *   norm_num,  int8 path: lambda = norm_num / 2^norm_shift, magnitude floored
+ *   norm_shift (0 < norm_num <= 2^norm_shift, 0 <= norm_shift <= 8).
+ *   offset_f32 float path: beta (>= 0).
+ *   norm_f32   float path: lambda (0 < lambda <= 1).
+ *   msg_sat    int8 path: Qm in [1, 127]; |Z_n' - L_mn'| saturates to Qm before
+ *              the minimum of Eq. (1)/(3).
+ *   max_iter   iteration cap (>= 0).  0 returns the channel decisions.
+ *   early_stop 1: a frame stops at the first k in 0..max_iter whose decisions
+ *              satisfy H x^T = 0 (checked before the first iteration too);
+ *              0: every frame runs max_iter iterations.
+ */
+typedef struct {
+  int32_t dtype;
+  int32_t form;
+  int32_t rule;
+  int32_t offset;
+  int32_t norm_num;
+  int32_t norm_shift;
+  float offset_f32;
+  float norm_f32;
+  int32_t msg_sat;
+  int32_t max_iter;
+  int32_t early_stop;
+  int32_t reserved;
+} ldpc_decode_params;
+
+/* Build a code from the check->variable adjacency N(m) of H (Section II).
+ *   row_ptr  host, [n_checks + 1], row_ptr[0] = 0, non-decreasing.
+ *   col_idx  host, [row_ptr[n_checks]]: the variables of check m are
+ *            col_idx[row_ptr[m] .. row_ptr[m+1]-1]; their order is the row
+ *            position used by the Section V index n~.
+ *   device   CUDA device ordinal that will run the decodes.
+ * Checks: n_vars >= 1, n_checks >= 1, every check degree in [2, 32], indices in
+ * [0, n_vars), no variable twice in a check; otherwise LDPC_ERR_INVALID_ARG.
+ * Variables of degree 0 or 1 are allowed.  On success *out owns device memory
+ * until ldpc_code_destroy.  Synchronous. */
+LDPC_API ldpc_status ldpc_code_create(ldpc_code **out, int32_t n_vars, int32_t n_checks,
+                             const int32_t *row_ptr, const int32_t *col_idx, int device);
+
+/* Release a code (NULL is accepted).  Synchronises the code's device first. */
+LDPC_API ldpc_status ldpc_code_destroy(ldpc_code *code);
+
+/* Sizes of a code: any output pointer may be NULL. */
+LDPC_API ldpc_status ldpc_code_info(const ldpc_code *code, int32_t *n_vars, int32_t *n_checks,
+                           int32_t *n_edges, int32_t *max_row_degree, int32_t *max_col_degree);
+
+/* Device workspace (bytes) that ldpc_decode_batch needs for this request;
+ * 0 when the chosen kernel keeps all per-frame state on chip. */
+LDPC_API ldpc_status ldpc_workspace_size(const ldpc_code *code, const ldpc_decode_params *params,
+                                int32_t n_frames, size_t *bytes);
+
+/* Decode a batch of frames (Sections III-V).
+ *   llr          device, frame-major [n_frames][n_vars] channel values Z0_n,
+ *                int8 or float32 per params->dtype.
+ *   hard_bits    device, [n_frames][ceil(n_vars/8)]: decision of variable n at
+ *                byte n>>3, bit n&7 (1 means x_n = 1, i.e. Z_n <= 0).
+ *   iters_used   device, [n_frames]: iterations run (the k at which H x^T = 0
+ *                was met with early_stop, else max_iter).
+ *   syndrome_ok  device, [n_frames]: 1 when the returned decisions satisfy H.
+ *   llr_out      device or NULL, [n_frames][n_vars] final posterior Z_n:
+ *                int16 for the int8 path, float32 for the float path.
+ *   workspace    device or NULL, at least ldpc_workspace_size() bytes,
+ *                256-byte aligned, not used by another call in flight.
+ * Returns LDPC_ERR_UNSUPPORTED when the int8 posterior could leave int16
+ * (128 + max_col_degree * msg_sat > 32767) or the code is too large for every
+ * kernel of this build. */
+LDPC_API ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_params *params,
+                              const void *llr, int32_t n_frames, uint8_t *hard_bits,
+                              int32_t *iters_used, uint8_t *syndrome_ok, void *llr_out,
+                              void *workspace, size_t ws_bytes, void *stream);
+
+/* Message describing the last failed call on this thread ("" if none). */
+LDPC_API const char *ldpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDPC_GB300_H */

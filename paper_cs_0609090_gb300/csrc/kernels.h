@@ -1,0 +1,35 @@
+// kernels.h -- host-side launch interface between the C ABI layer and the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ldpc {
+
+// Launch configuration of the frame-resident ("on-chip") kernel: every CTA
+// keeps G frames' posteriors, accumulators and check state in shared memory for
+// all iterations.
+struct OnchipPlan {
+  int G = 0;            // frames per CTA (even)
+  int threads = 0;      // threads per CTA
+  size_t smem = 0;      // dynamic shared memory bytes
+  int grid = 0;         // CTAs launched (persistent over frame groups)
+  int n_groups = 0;
+};
+
+// Fills *plan for an int8 decode (form: 0 fixed, 1 one-bit).  Returns false if
+// no G fits in shared memory.
+bool onchip_int8_plan(const DevCode& c, int form, int32_t n_frames, int sm_count,
+                      size_t smem_optin, int max_row_deg, OnchipPlan* plan);
+
+// Sets plan->grid from the occupancy of the chosen instantiation (persistent grid).
+cudaError_t onchip_int8_occupancy(int form, int sm_count, OnchipPlan* plan);
+
+cudaError_t onchip_int8_launch(const DevCode& c, const IntRule& r, int form, const OnchipPlan& plan,
+                               const int8_t* llr, int32_t n_frames, int32_t max_iter,
+                               int32_t early_stop, uint8_t* bits, int32_t* iters, uint8_t* ok,
+                               int16_t* zout, cudaStream_t stream);
+
+}  // namespace ldpc

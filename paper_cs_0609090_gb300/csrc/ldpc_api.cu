@@ -1,0 +1,276 @@
+// ldpc_api.cu -- the C ABI (include/ldpc_gb300.h): argument checks, the device
+// copy of a code, kernel selection and error reporting.  No kernel logic here.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ldpc_gb300.h"
+#include "kernels.h"
+
+struct ldpc_code {
+  int device = 0;
+  int32_t N = 0, M = 0, E = 0;
+  int32_t max_row_deg = 0, max_col_deg = 0;
+  int32_t* d_rp = nullptr;
+  int32_t* d_ci = nullptr;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ldpc_status fail(ldpc_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+ldpc_status fail(ldpc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+ldpc_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error so later calls start clean
+  return fail(e == cudaErrorMemoryAllocation ? LDPC_ERR_OOM : LDPC_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+ldpc::DevCode view(const ldpc_code* c) {
+  ldpc::DevCode v;
+  v.N = c->N;
+  v.M = c->M;
+  v.E = c->E;
+  v.rp = c->d_rp;
+  v.ci = c->d_ci;
+  return v;
+}
+
+ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
+  if (p->dtype != LDPC_DTYPE_INT8 && p->dtype != LDPC_DTYPE_F32)
+    return fail(LDPC_ERR_INVALID_ARG, "dtype %d is not LDPC_DTYPE_INT8/F32", p->dtype);
+  if (p->form < LDPC_FORM_SS_FIXED || p->form > LDPC_FORM_TWO_SCAN)
+    return fail(LDPC_ERR_INVALID_ARG, "form %d is not a known LDPC_FORM_*", p->form);
+  if (p->rule < LDPC_RULE_PLAIN || p->rule > LDPC_RULE_NORMALIZED)
+    return fail(LDPC_ERR_INVALID_ARG, "rule %d is not a known LDPC_RULE_*", p->rule);
+  if (p->max_iter < 0) return fail(LDPC_ERR_INVALID_ARG, "max_iter %d < 0", p->max_iter);
+  if (p->early_stop != 0 && p->early_stop != 1)
+    return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");
+  if (p->dtype == LDPC_DTYPE_INT8) {
+    if (p->msg_sat < 1 || p->msg_sat > 127)
+      return fail(LDPC_ERR_INVALID_ARG, "msg_sat %d outside [1, 127]", p->msg_sat);
+    if (p->rule == LDPC_RULE_OFFSET && (p->offset < 0 || p->offset > 127))
+      return fail(LDPC_ERR_INVALID_ARG, "offset %d outside [0, 127]", p->offset);
+    if (p->rule == LDPC_RULE_NORMALIZED &&
+        (p->norm_shift < 0 || p->norm_shift > 8 || p->norm_num <= 0 || p->norm_num > (1 << p->norm_shift)))
+      return fail(LDPC_ERR_INVALID_ARG, "normalization %d/2^%d is not in (0, 1]", p->norm_num,
+                  p->norm_shift);
+    // The posterior is held exactly in int16: |Z| <= 128 + max_col_degree * Qm.
+    if (128 + (int64_t)c->max_col_deg * p->msg_sat > 32767)
+      return fail(LDPC_ERR_UNSUPPORTED,
+                  "posterior bound 128 + %d * %d exceeds int16; lower msg_sat or the column degree",
+                  c->max_col_deg, p->msg_sat);
+  } else {
+    if (p->rule == LDPC_RULE_OFFSET && !(p->offset_f32 >= 0.0f))
+      return fail(LDPC_ERR_INVALID_ARG, "offset_f32 must be >= 0");
+    if (p->rule == LDPC_RULE_NORMALIZED && !(p->norm_f32 > 0.0f && p->norm_f32 <= 1.0f))
+      return fail(LDPC_ERR_INVALID_ARG, "norm_f32 must be in (0, 1]");
+  }
+  return LDPC_OK;
+}
+
+// Which kernel serves a request; ws = workspace bytes it needs.
+struct Choice {
+  enum Kind { NONE, ONCHIP_INT8 } kind = NONE;
+  ldpc::OnchipPlan onchip;
+  size_t ws = 0;
+};
+
+ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_frames, Choice* ch) {
+  const ldpc::DevCode v = view(c);
+  if (p->dtype == LDPC_DTYPE_INT8 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED)) {
+    const int form = p->form == LDPC_FORM_SS_1BIT ? 1 : 0;
+    if (ldpc::onchip_int8_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
+      ch->kind = Choice::ONCHIP_INT8;
+      ch->ws = 0;
+      return LDPC_OK;
+    }
+    return fail(LDPC_ERR_UNSUPPORTED, "code (N=%d, M=%d, E=%d) does not fit the frame-resident kernel",
+                c->N, c->M, c->E);
+  }
+  return fail(LDPC_ERR_UNSUPPORTED, "dtype %d / form %d is not available in this build", p->dtype, p->form);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ldpc_last_error(void) { return g_last_error.c_str(); }
+
+ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, const int32_t* row_ptr,
+                             const int32_t* col_idx, int device) {
+  g_last_error.clear();
+  if (out == nullptr) return fail(LDPC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (row_ptr == nullptr) return fail(LDPC_ERR_INVALID_ARG, "row_ptr is NULL");
+  if (n_vars < 1 || n_checks < 1) return fail(LDPC_ERR_INVALID_ARG, "n_vars and n_checks must be >= 1");
+  if (row_ptr[0] != 0) return fail(LDPC_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+  int32_t max_row = 0;
+  for (int32_t m = 0; m < n_checks; ++m) {
+    const int64_t d = (int64_t)row_ptr[m + 1] - row_ptr[m];
+    if (d < 2 || d > 32)
+      return fail(LDPC_ERR_INVALID_ARG, "check %d has degree %lld; degrees must be in [2, 32]", m, (long long)d);
+    if (d > max_row) max_row = (int32_t)d;
+  }
+  const int32_t E = row_ptr[n_checks];
+  if (col_idx == nullptr) return fail(LDPC_ERR_INVALID_ARG, "col_idx is NULL");
+  std::vector<int32_t> col_deg((size_t)n_vars, 0);
+  std::vector<int32_t> seen((size_t)n_vars, -1);
+  for (int32_t m = 0; m < n_checks; ++m) {
+    for (int32_t e = row_ptr[m]; e < row_ptr[m + 1]; ++e) {
+      const int32_t n = col_idx[e];
+      if (n < 0 || n >= n_vars)
+        return fail(LDPC_ERR_INVALID_ARG, "col_idx[%d] = %d outside [0, %d)", e, n, n_vars);
+      if (seen[(size_t)n] == m)
+        return fail(LDPC_ERR_INVALID_ARG, "variable %d appears twice in check %d", n, m);
+      seen[(size_t)n] = m;
+      col_deg[(size_t)n]++;
+    }
+  }
+  int32_t max_col = 0;
+  for (int32_t d : col_deg) max_col = d > max_col ? d : max_col;
+
+  int n_dev = 0;
+  cudaError_t err = cudaGetDeviceCount(&n_dev);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGetDeviceCount");
+  if (device < 0 || device >= n_dev) return fail(LDPC_ERR_INVALID_ARG, "device %d of %d", device, n_dev);
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(LDPC_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+
+  ldpc_code* c = new ldpc_code();
+  c->device = device;
+  c->N = n_vars;
+  c->M = n_checks;
+  c->E = E;
+  c->max_row_deg = max_row;
+  c->max_col_deg = max_col;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  c->sm_count = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = (size_t)v;
+  if ((err = cudaMalloc(&c->d_rp, sizeof(int32_t) * ((size_t)n_checks + 1))) != cudaSuccess ||
+      (err = cudaMalloc(&c->d_ci, sizeof(int32_t) * (size_t)E)) != cudaSuccess ||
+      (err = cudaMemcpy(c->d_rp, row_ptr, sizeof(int32_t) * ((size_t)n_checks + 1), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (err = cudaMemcpy(c->d_ci, col_idx, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(c->d_rp);
+    cudaFree(c->d_ci);
+    delete c;
+    return cuda_fail(err, "ldpc_code_create device copy");
+  }
+  *out = c;
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_code_destroy(ldpc_code* code) {
+  g_last_error.clear();
+  if (code == nullptr) return LDPC_OK;
+  DeviceGuard guard(code->device);
+  cudaDeviceSynchronize();
+  cudaFree(code->d_rp);
+  cudaFree(code->d_ci);
+  delete code;
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_code_info(const ldpc_code* code, int32_t* n_vars, int32_t* n_checks, int32_t* n_edges,
+                           int32_t* max_row_degree, int32_t* max_col_degree) {
+  g_last_error.clear();
+  if (code == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code is NULL");
+  if (n_vars) *n_vars = code->N;
+  if (n_checks) *n_checks = code->M;
+  if (n_edges) *n_edges = code->E;
+  if (max_row_degree) *max_row_degree = code->max_row_deg;
+  if (max_col_degree) *max_col_degree = code->max_col_deg;
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_workspace_size(const ldpc_code* code, const ldpc_decode_params* params, int32_t n_frames,
+                                size_t* bytes) {
+  g_last_error.clear();
+  if (code == nullptr || params == nullptr || bytes == nullptr)
+    return fail(LDPC_ERR_INVALID_ARG, "code, params and bytes must be non-NULL");
+  if (n_frames < 0) return fail(LDPC_ERR_INVALID_ARG, "n_frames %d < 0", n_frames);
+  *bytes = 0;
+  ldpc_status s = check_params(code, params);
+  if (s != LDPC_OK) return s;
+  if (n_frames == 0) return LDPC_OK;
+  Choice ch;
+  s = choose(code, params, n_frames, &ch);
+  if (s != LDPC_OK) return s;
+  *bytes = ch.ws;
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* params, const void* llr,
+                              int32_t n_frames, uint8_t* hard_bits, int32_t* iters_used, uint8_t* syndrome_ok,
+                              void* llr_out, void* workspace, size_t ws_bytes, void* stream) {
+  g_last_error.clear();
+  if (code == nullptr || params == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code and params must be non-NULL");
+  if (n_frames < 0) return fail(LDPC_ERR_INVALID_ARG, "n_frames %d < 0", n_frames);
+  ldpc_status s = check_params(code, params);
+  if (s != LDPC_OK) return s;
+  if (n_frames == 0) return LDPC_OK;
+  if (llr == nullptr || hard_bits == nullptr || iters_used == nullptr || syndrome_ok == nullptr)
+    return fail(LDPC_ERR_INVALID_ARG, "llr, hard_bits, iters_used and syndrome_ok must be non-NULL");
+  Choice ch;
+  s = choose(code, params, n_frames, &ch);
+  if (s != LDPC_OK) return s;
+  if (ch.ws > 0 && (workspace == nullptr || ws_bytes < ch.ws))
+    return fail(LDPC_ERR_INVALID_ARG, "workspace of %zu bytes needed, %zu given", ch.ws,
+                workspace ? ws_bytes : (size_t)0);
+  if (workspace != nullptr && ((uintptr_t)workspace & 255u) != 0)
+    return fail(LDPC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  DeviceGuard guard(code->device);
+  if (!guard.ok) return fail(LDPC_ERR_CUDA, "cudaSetDevice(%d) failed", code->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const ldpc::DevCode v = view(code);
+  cudaError_t err = cudaSuccess;
+  if (ch.kind == Choice::ONCHIP_INT8) {
+    ldpc::IntRule r;
+    r.rule = params->rule;
+    r.beta = params->offset;
+    r.num = params->norm_num;
+    r.shift = params->norm_shift;
+    r.qm = params->msg_sat;
+    const int form = params->form == LDPC_FORM_SS_1BIT ? 1 : 0;
+    err = ldpc::onchip_int8_occupancy(form, code->sm_count, &ch.onchip);
+    if (err == cudaSuccess)
+      err = ldpc::onchip_int8_launch(v, r, form, ch.onchip, static_cast<const int8_t*>(llr), n_frames,
+                                     params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
+                                     static_cast<int16_t*>(llr_out), st);
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "ldpc_decode_batch launch");
+  return LDPC_OK;
+}
+
+}  // extern "C"

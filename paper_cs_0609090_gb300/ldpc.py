@@ -1,0 +1,192 @@
+"""Thin Python binding over the C ABI in include/ldpc_gb300.h.
+
+The functions keep the C names and only marshal arguments: torch tensors are
+passed as ``data_ptr()`` and the current CUDA stream as its handle.  Every step
+of decoding runs in the CUDA kernels of libldpc_gb300.so; if that library is
+missing, importing this module raises ImportError (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libldpc_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+LDPC_OK, LDPC_ERR_INVALID_ARG, LDPC_ERR_UNSUPPORTED, LDPC_ERR_CUDA, LDPC_ERR_OOM, LDPC_ERR_TIMEOUT = range(6)
+LDPC_DTYPE_INT8, LDPC_DTYPE_F32 = 0, 1
+LDPC_FORM_SS_FIXED, LDPC_FORM_SS_1BIT, LDPC_FORM_TWO_SCAN = 0, 1, 2
+LDPC_RULE_PLAIN, LDPC_RULE_OFFSET, LDPC_RULE_NORMALIZED = 0, 1, 2
+
+DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_F32}
+FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
+RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED}
+
+# Every symbol include/ldpc_gb300.h declares.
+EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",
+           "ldpc_decode_batch", "ldpc_last_error")
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: status {status}: {ldpc_last_error()}")
+
+
+class ldpc_decode_params(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("form", ctypes.c_int32), ("rule", ctypes.c_int32),
+                ("offset", ctypes.c_int32), ("norm_num", ctypes.c_int32), ("norm_shift", ctypes.c_int32),
+                ("offset_f32", ctypes.c_float), ("norm_f32", ctypes.c_float),
+                ("msg_sat", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("early_stop", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_lib.ldpc_code_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int]
+_lib.ldpc_code_destroy.argtypes = [_P]
+_lib.ldpc_code_info.argtypes = [_P, _P, _P, _P, _P, _P]
+_lib.ldpc_workspace_size.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_size_t)]
+_lib.ldpc_decode_batch.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), _P, ctypes.c_int32, _P, _P, _P,
+                                   _P, _P, ctypes.c_size_t, _P]
+_lib.ldpc_last_error.restype = ctypes.c_char_p
+for _f in EXPORTS[:-1]:
+    getattr(_lib, _f).restype = ctypes.c_int32
+
+
+def _check(status: int, where: str):
+    if status != LDPC_OK:
+        raise LdpcError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(_P)
+    return _P(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if hasattr(stream, "cuda_stream"):
+        return _P(stream.cuda_stream)
+    return _P(int(stream))
+
+
+def ldpc_last_error() -> str:
+    return (_lib.ldpc_last_error() or b"").decode()
+
+
+def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=3, norm_shift=2,
+                offset_f32=0.0, norm_f32=0.75, msg_sat=127, max_iter=20, early_stop=1,
+                norm=None, **_ignored) -> ldpc_decode_params:
+    """Builds ldpc_decode_params from names ('int8'/'f32', 'ss_fixed'/'ss_1bit'/'two_scan',
+    'plain'/'offset'/'normalized').  ``norm`` is an alias for norm_f32."""
+    if norm is not None:
+        norm_f32 = norm
+    return ldpc_decode_params(DTYPES[dtype] if isinstance(dtype, str) else dtype,
+                              FORMS[form] if isinstance(form, str) else form,
+                              RULES[rule] if isinstance(rule, str) else rule,
+                              int(offset), int(norm_num), int(norm_shift), float(offset_f32),
+                              float(norm_f32), int(msg_sat), int(max_iter), int(early_stop), 0)
+
+
+def ldpc_code_create(n_vars: int, n_checks: int, row_ptr, col_idx, device: int = 0) -> int:
+    """Returns an opaque handle (int).  row_ptr/col_idx: host int32 arrays."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h = _P()
+    _check(_lib.ldpc_code_create(ctypes.byref(h), int(n_vars), int(n_checks), _ptr(rp), _ptr(ci), int(device)),
+           "ldpc_code_create")
+    return h.value
+
+
+def ldpc_code_destroy(code: int) -> None:
+    _check(_lib.ldpc_code_destroy(_P(code)), "ldpc_code_destroy")
+
+
+def ldpc_code_info(code: int) -> dict:
+    vals = [ctypes.c_int32() for _ in range(5)]
+    _check(_lib.ldpc_code_info(_P(code), *[ctypes.byref(v) for v in vals]), "ldpc_code_info")
+    return dict(zip(("n_vars", "n_checks", "n_edges", "max_row_degree", "max_col_degree"),
+                    (v.value for v in vals)))
+
+
+def ldpc_workspace_size(code: int, params: ldpc_decode_params, n_frames: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib.ldpc_workspace_size(_P(code), ctypes.byref(params), int(n_frames), ctypes.byref(out)),
+           "ldpc_workspace_size")
+    return out.value
+
+
+def ldpc_decode_batch(code: int, params: ldpc_decode_params, llr, n_frames: int, hard_bits, iters_used,
+                      syndrome_ok, llr_out=None, workspace=None, ws_bytes: int = 0, stream=None) -> None:
+    """All tensors are CUDA tensors of the layouts documented in the header."""
+    _check(_lib.ldpc_decode_batch(_P(code), ctypes.byref(params), _ptr(llr), int(n_frames), _ptr(hard_bits),
+                                  _ptr(iters_used), _ptr(syndrome_ok), _ptr(llr_out), _ptr(workspace),
+                                  int(ws_bytes), _stream_handle(stream)), "ldpc_decode_batch")
+
+
+class Code:
+    """Owning wrapper of an ldpc_code handle."""
+
+    def __init__(self, n_vars, n_checks, row_ptr, col_idx, device=0):
+        self.handle = ldpc_code_create(n_vars, n_checks, row_ptr, col_idx, device)
+        self.n_vars, self.n_checks = int(n_vars), int(n_checks)
+        self.device = device
+
+    @classmethod
+    def from_inputs(cls, code, device=0):
+        return cls(code.n_vars, code.n_checks, code.row_ptr, code.col_idx, device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ldpc_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decode(code: Code, llr, params: ldpc_decode_params, want_llr: bool = False, stream=None,
+           workspace=None):
+    """Allocates outputs with torch on llr's device and calls ldpc_decode_batch.
+    Returns (hard_bits uint8 [F, ceil(N/8)], iters int32 [F], ok uint8 [F], llr_out or None)."""
+    import torch
+    F, N = llr.shape
+    dev = llr.device
+    bits = torch.empty((F, (N + 7) // 8), dtype=torch.uint8, device=dev)
+    iters = torch.empty(F, dtype=torch.int32, device=dev)
+    ok = torch.empty(F, dtype=torch.uint8, device=dev)
+    zo = None
+    if want_llr:
+        zo = torch.empty((F, N), dtype=torch.int16 if params.dtype == LDPC_DTYPE_INT8 else torch.float32,
+                         device=dev)
+    ws_bytes = ldpc_workspace_size(code.handle, params, F)
+    if ws_bytes and workspace is None:
+        workspace = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    ws_ptr = None
+    if ws_bytes:
+        base = workspace.data_ptr()
+        ws_ptr = _P((base + 255) & ~255)
+    _check(_lib.ldpc_decode_batch(_P(code.handle), ctypes.byref(params), _ptr(llr), int(F), _ptr(bits),
+                                  _ptr(iters), _ptr(ok), _ptr(zo), ws_ptr, int(ws_bytes),
+                                  _stream_handle(stream)), "ldpc_decode_batch")
+    return bits, iters, ok, zo
+
+
+def unpack_bits(hard_bits: np.ndarray, n_vars: int) -> np.ndarray:
+    """[F, ceil(N/8)] packed (bit n at byte n>>3, bit n&7) -> [F, N] uint8."""
+    return np.unpackbits(np.asarray(hard_bits, dtype=np.uint8), axis=1, bitorder="little")[:, :n_vars]

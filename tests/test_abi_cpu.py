@@ -1,0 +1,88 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every symbol that
+include/*.h declares, and rejects malformed requests before touching CUDA."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names |= set(re.findall(r"LDPC_API\s+[\w\s\*]*?\b(ldpc_\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_cs_0609090_gb300 import ldpc
+    return ldpc
+
+
+def test_library_exports_every_declared_symbol(L):
+    declared = _declared_symbols()
+    assert declared, "no LDPC_API declarations found"
+    lib = ctypes.CDLL(L.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(L.EXPORTS)
+
+
+def test_params_struct_layout(L):
+    # 12 four-byte fields, as in ldpc_decode_params
+    assert ctypes.sizeof(L.ldpc_decode_params) == 48
+
+
+def _create_raw(L, n_vars, n_checks, rp, ci):
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(rp, np.int32)
+    ci = np.ascontiguousarray(ci, np.int32)
+    st = L._lib.ldpc_code_create(ctypes.byref(h), n_vars, n_checks, rp.ctypes.data_as(ctypes.c_void_p),
+                                 ci.ctypes.data_as(ctypes.c_void_p), 0)
+    return st, h
+
+
+def test_create_rejects_malformed_h(L):
+    ok_rp, ok_ci = [0, 4, 8, 12], [0, 1, 3, 4, 0, 2, 3, 5, 1, 2, 3, 6]
+    assert _create_raw(L, 7, 3, [1, 4, 8, 12], ok_ci)[0] == L.LDPC_ERR_INVALID_ARG       # row_ptr[0] != 0
+    assert "row_ptr[0]" in L.ldpc_last_error()
+    assert _create_raw(L, 7, 3, [0, 1, 8, 12], ok_ci)[0] == L.LDPC_ERR_INVALID_ARG       # degree 1
+    assert _create_raw(L, 7, 3, ok_rp, [0, 1, 3, 9] + ok_ci[4:])[0] == L.LDPC_ERR_INVALID_ARG  # index
+    assert _create_raw(L, 7, 3, ok_rp, [0, 1, 1, 4] + ok_ci[4:])[0] == L.LDPC_ERR_INVALID_ARG  # repeat
+    assert "twice" in L.ldpc_last_error()
+    assert _create_raw(L, 0, 3, ok_rp, ok_ci)[0] == L.LDPC_ERR_INVALID_ARG
+    big = [0, 33]
+    assert _create_raw(L, 40, 1, big, list(range(33)))[0] == L.LDPC_ERR_INVALID_ARG     # degree 33
+    st = L._lib.ldpc_code_create(None, 7, 3, None, None, 0)
+    assert st == L.LDPC_ERR_INVALID_ARG
+
+
+def test_null_arguments(L):
+    p = L.make_params()
+    assert L._lib.ldpc_decode_batch(None, ctypes.byref(p), None, 1, None, None, None, None, None, 0,
+                                    None) == L.LDPC_ERR_INVALID_ARG
+    out = ctypes.c_size_t()
+    assert L._lib.ldpc_workspace_size(None, ctypes.byref(p), 1, ctypes.byref(out)) == L.LDPC_ERR_INVALID_ARG
+    assert L._lib.ldpc_code_destroy(None) == L.LDPC_OK
+    assert L._lib.ldpc_code_info(None, None, None, None, None, None) == L.LDPC_ERR_INVALID_ARG
+
+
+def test_valid_code_without_gpu_reports_cuda_error(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, h = _create_raw(L, 7, 3, [0, 4, 8, 12], [0, 1, 3, 4, 0, 2, 3, 5, 1, 2, 3, 6])
+    assert st in (L.LDPC_ERR_CUDA, L.LDPC_ERR_INVALID_ARG)
+    assert h.value is None
+    assert L.ldpc_last_error() != ""
+
+
+def test_unpack_bits_layout(L):
+    hb = np.array([[0b00000101, 0b1]], dtype=np.uint8)
+    assert L.unpack_bits(hb, 9).tolist() == [[1, 0, 1, 0, 0, 0, 0, 0, 1]]
