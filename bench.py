@@ -174,7 +174,7 @@ def run_reference(args, world, rank):
         return 0
     w = I.make_workload(args.workload)
     w.params["early_stop"] = 0
-    budget = float(os.environ.get("BENCH_REF_BUDGET_S", "8"))
+    budget = float(os.environ.get("BENCH_REF_BUDGET_S", "4"))
     per_step = []
     info = None
     for s in range(args.warmup + args.steps):
@@ -204,6 +204,7 @@ def main():
     ap.add_argument("--workload", default="qc_n7493")
     ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -220,7 +221,13 @@ def main():
     w.params["early_stop"] = 0
     F, N, K = w.n_frames, w.code.n_vars, w.K
     code = ldpc.Code.from_inputs(w.code, device=local)
-    params = ldpc.make_params(form=args.form, **w.params)
+    params = ldpc.make_params(form=args.form, kernel=args.kernel, **w.params)
+    kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel"}.get(args.kernel)
+    if kname is None:
+        info = ldpc.ldpc_code_info(code.handle)
+        half_ok = info["max_row_degree"] <= 16 and \
+            128 + (info["max_col_degree"] + 1) * w.params["msg_sat"] <= 2048
+        kname = "onchip_h2_kernel" if half_ok else "onchip_int8_kernel"
     llr = torch.from_numpy(w.q0).to(dev)
     bits = torch.empty((F, (N + 7) // 8), dtype=torch.uint8, device=dev)
     iters = torch.empty(F, dtype=torch.int32, device=dev)
@@ -302,19 +309,19 @@ def main():
     peaks = measured_peaks()
     achieved = ab["per_launch"] / (ms_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic("onchip_int8_kernel",
-                                                                                  w.name, args.form),
+                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(kname, w.name, args.form),
                 "peak_source": peaks["source"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": ab["per_launch"],
                 "bytes_per_frame_iter": ab["per_frame_iter"],
-                "kernel": "onchip_int8_kernel", "kernel_ms": ms_step}
+                "kernel": kname, "kernel_ms": ms_step}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int8", "data": "synthetic",
             "config": {"workload": w.name, "form": args.form, "n_frames": F, "iters": w.params["max_iter"],
                        "N": N, "M": w.code.n_checks, "E": w.code.n_edges, "K": K,
                        "ebn0_db": w.ebn0_db, "rule": w.params["rule"], "early_stop": 0,
-                       "l2": "flushed between timed steps (256 MB write)", "frames_per_rank": F},
+                       "l2": "flushed between timed steps (256 MB write)", "frames_per_rank": F,
+                       "kernel": args.kernel},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(w.q0.nbytes),
                     "d2h_bytes_per_step": int(bits.numel() + iters.numel() * 4 + ok.numel())},
             "gpu_launches": args.steps,

@@ -76,6 +76,15 @@ enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2 };
  *   early_stop 1: a frame stops at the first k in 0..max_iter whose decisions
  *              satisfy H x^T = 0 (checked before the first iteration too);
  *              0: every frame runs max_iter iterations.
+ *   kernel     LDPC_KERNEL_AUTO (0) lets the library choose; otherwise forces one
+ *              implementation (results are identical; LDPC_ERR_UNSUPPORTED if the
+ *              forced kernel cannot run this request):
+ *                LDPC_KERNEL_ONCHIP_INT   frame-resident, 32-bit integer lanes
+ *                LDPC_KERNEL_ONCHIP_HALF  frame-resident, two frames per packed
+ *                                         binary16 instruction (exact: needs row
+ *                                         degree <= 16 and
+ *                                         128 + (max_col_degree + 1) * msg_sat <= 2048
+ *                                         and n_vars <= 65535)
  */
 typedef struct {
   int32_t dtype;
@@ -89,8 +98,10 @@ typedef struct {
   int32_t msg_sat;
   int32_t max_iter;
   int32_t early_stop;
-  int32_t reserved;
+  int32_t kernel;
 } ldpc_decode_params;
+
+enum { LDPC_KERNEL_AUTO = 0, LDPC_KERNEL_ONCHIP_INT = 1, LDPC_KERNEL_ONCHIP_HALF = 2 };
 
 /* Build a code from the check->variable adjacency N(m) of H (Section II).
  *   row_ptr  host, [n_checks + 1], row_ptr[0] = 0, non-decreasing.

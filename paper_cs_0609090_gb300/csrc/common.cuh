@@ -10,6 +10,18 @@ struct DevCode {
   int32_t N, M, E;
   const int32_t* __restrict__ rp;  // [M+1]
   const int32_t* __restrict__ ci;  // [E]
+  const int32_t* __restrict__ cdeg;  // [N] number of checks of each variable, |M(n)|
+  // The same adjacency transposed to edge-slot-major order for coalesced loads:
+  // variable of position j of check m at ell[j * M + m] (j < ell_w, padded with
+  // the check's last variable); uint16 when N <= 65535, else int32.
+  const uint16_t* __restrict__ ell16;
+  const int32_t* __restrict__ ell32;
+  const uint8_t* __restrict__ rdeg;  // [M] check degrees |N(m)|
+  int32_t ell_w;
+  __device__ __forceinline__ int col(int j, int m) const {
+    return ell16 != nullptr ? (int)__ldg(ell16 + (size_t)j * M + m) : __ldg(ell32 + (size_t)j * M + m);
+  }
+  __device__ __forceinline__ int deg(int m) const { return (int)__ldg(rdeg + m); }
 };
 
 // Magnitude modification of Section III applied to integer magnitudes:

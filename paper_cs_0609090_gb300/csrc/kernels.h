@@ -17,6 +17,8 @@ struct OnchipPlan {
   size_t smem = 0;      // dynamic shared memory bytes
   int grid = 0;         // CTAs launched (persistent over frame groups)
   int n_groups = 0;
+  int dmax = 0;         // unrolled row-degree bound (packed-half kernel)
+  bool sidx = false;    // column table copied into shared memory
 };
 
 // Fills *plan for an int8 decode (form: 0 fixed, 1 one-bit).  Returns false if
@@ -31,5 +33,14 @@ cudaError_t onchip_int8_launch(const DevCode& c, const IntRule& r, int form, con
                                const int8_t* llr, int32_t n_frames, int32_t max_iter,
                                int32_t early_stop, uint8_t* bits, int32_t* iters, uint8_t* ok,
                                int16_t* zout, cudaStream_t stream);
+
+// Packed binary16 variant (two frames per instruction, exact for integers < 2048).
+bool onchip_h2_eligible(int n_vars, int max_row_deg, int max_col_deg, int qm);
+bool onchip_h2_plan(const DevCode& c, int form, int32_t n_frames, int sm_count, size_t smem_optin,
+                    int max_row_deg, OnchipPlan* plan);
+// Sets plan.grid from occupancy; launches unless occupancy_only.
+cudaError_t onchip_h2_launch(const DevCode& c, const IntRule& r, int form, OnchipPlan& plan, int sm_count,
+                             const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
+                             int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t stream, bool occupancy_only);
 
 }  // namespace ldpc

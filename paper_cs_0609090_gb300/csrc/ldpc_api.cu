@@ -15,6 +15,11 @@ struct ldpc_code {
   int32_t max_row_deg = 0, max_col_deg = 0;
   int32_t* d_rp = nullptr;
   int32_t* d_ci = nullptr;
+  int32_t* d_cdeg = nullptr;
+  uint16_t* d_ell16 = nullptr;
+  int32_t* d_ell32 = nullptr;
+  uint8_t* d_rdeg = nullptr;
+  int32_t ell_w = 0;
   int sm_count = 0;
   size_t smem_optin = 0;
 };
@@ -61,6 +66,11 @@ ldpc::DevCode view(const ldpc_code* c) {
   v.E = c->E;
   v.rp = c->d_rp;
   v.ci = c->d_ci;
+  v.cdeg = c->d_cdeg;
+  v.ell16 = c->d_ell16;
+  v.ell32 = c->d_ell32;
+  v.rdeg = c->d_rdeg;
+  v.ell_w = c->ell_w;
   return v;
 }
 
@@ -74,6 +84,8 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   if (p->max_iter < 0) return fail(LDPC_ERR_INVALID_ARG, "max_iter %d < 0", p->max_iter);
   if (p->early_stop != 0 && p->early_stop != 1)
     return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");
+  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_ONCHIP_HALF)
+    return fail(LDPC_ERR_INVALID_ARG, "kernel %d is not a known LDPC_KERNEL_*", p->kernel);
   if (p->dtype == LDPC_DTYPE_INT8) {
     if (p->msg_sat < 1 || p->msg_sat > 127)
       return fail(LDPC_ERR_INVALID_ARG, "msg_sat %d outside [1, 127]", p->msg_sat);
@@ -99,7 +111,7 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
 
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
-  enum Kind { NONE, ONCHIP_INT8 } kind = NONE;
+  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2 } kind = NONE;
   ldpc::OnchipPlan onchip;
   size_t ws = 0;
 };
@@ -108,13 +120,22 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
   const ldpc::DevCode v = view(c);
   if (p->dtype == LDPC_DTYPE_INT8 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED)) {
     const int form = p->form == LDPC_FORM_SS_1BIT ? 1 : 0;
-    if (ldpc::onchip_int8_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
+    const bool want_half = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF;
+    const bool want_int = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_INT;
+    if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat) &&
+        ldpc::onchip_h2_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
+      ch->kind = Choice::ONCHIP_H2;
+      ch->ws = 0;
+      return LDPC_OK;
+    }
+    if (want_int && ldpc::onchip_int8_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_INT8;
       ch->ws = 0;
       return LDPC_OK;
     }
-    return fail(LDPC_ERR_UNSUPPORTED, "code (N=%d, M=%d, E=%d) does not fit the frame-resident kernel",
-                c->N, c->M, c->E);
+    return fail(LDPC_ERR_UNSUPPORTED, "code (N=%d, M=%d, E=%d, row degree <= %d, column degree <= %d) "
+                "cannot run on the requested frame-resident kernel (%d)",
+                c->N, c->M, c->E, c->max_row_deg, c->max_col_deg, p->kernel);
   }
   return fail(LDPC_ERR_UNSUPPORTED, "dtype %d / form %d is not available in this build", p->dtype, p->form);
 }
@@ -157,6 +178,20 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   }
   int32_t max_col = 0;
   for (int32_t d : col_deg) max_col = d > max_col ? d : max_col;
+  // edge-slot-major copy of N(m), padded with each check's last variable
+  const bool narrow = n_vars <= 65535;
+  std::vector<uint16_t> ell16(narrow ? (size_t)max_row * n_checks : 0);
+  std::vector<int32_t> ell32(narrow ? 0 : (size_t)max_row * n_checks);
+  std::vector<uint8_t> rdeg((size_t)n_checks);
+  for (int32_t m = 0; m < n_checks; ++m) {
+    const int32_t d = row_ptr[m + 1] - row_ptr[m];
+    rdeg[(size_t)m] = (uint8_t)d;
+    for (int32_t j = 0; j < max_row; ++j) {
+      const int32_t n = col_idx[row_ptr[m] + (j < d ? j : d - 1)];
+      if (narrow) ell16[(size_t)j * n_checks + m] = (uint16_t)n;
+      else ell32[(size_t)j * n_checks + m] = n;
+    }
+  }
 
   int n_dev = 0;
   cudaError_t err = cudaGetDeviceCount(&n_dev);
@@ -172,6 +207,7 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   c->E = E;
   c->max_row_deg = max_row;
   c->max_col_deg = max_col;
+  c->ell_w = max_row;
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
   c->sm_count = v;
@@ -179,11 +215,26 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   c->smem_optin = (size_t)v;
   if ((err = cudaMalloc(&c->d_rp, sizeof(int32_t) * ((size_t)n_checks + 1))) != cudaSuccess ||
       (err = cudaMalloc(&c->d_ci, sizeof(int32_t) * (size_t)E)) != cudaSuccess ||
+      (err = cudaMalloc(&c->d_cdeg, sizeof(int32_t) * (size_t)n_vars)) != cudaSuccess ||
+      (err = cudaMemcpy(c->d_cdeg, col_deg.data(), sizeof(int32_t) * (size_t)n_vars, cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (err = cudaMalloc(&c->d_rdeg, (size_t)n_checks)) != cudaSuccess ||
+      (err = cudaMemcpy(c->d_rdeg, rdeg.data(), (size_t)n_checks, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (narrow && (err = cudaMalloc(&c->d_ell16, sizeof(uint16_t) * ell16.size())) != cudaSuccess) ||
+      (narrow && (err = cudaMemcpy(c->d_ell16, ell16.data(), sizeof(uint16_t) * ell16.size(),
+                                   cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!narrow && (err = cudaMalloc(&c->d_ell32, sizeof(int32_t) * ell32.size())) != cudaSuccess) ||
+      (!narrow && (err = cudaMemcpy(c->d_ell32, ell32.data(), sizeof(int32_t) * ell32.size(),
+                                    cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (err = cudaMemcpy(c->d_rp, row_ptr, sizeof(int32_t) * ((size_t)n_checks + 1), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (err = cudaMemcpy(c->d_ci, col_idx, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(c->d_rp);
     cudaFree(c->d_ci);
+    cudaFree(c->d_cdeg);
+    cudaFree(c->d_rdeg);
+    cudaFree(c->d_ell16);
+    cudaFree(c->d_ell32);
     delete c;
     return cuda_fail(err, "ldpc_code_create device copy");
   }
@@ -198,6 +249,10 @@ ldpc_status ldpc_code_destroy(ldpc_code* code) {
   cudaDeviceSynchronize();
   cudaFree(code->d_rp);
   cudaFree(code->d_ci);
+  cudaFree(code->d_cdeg);
+  cudaFree(code->d_rdeg);
+  cudaFree(code->d_ell16);
+  cudaFree(code->d_ell32);
   delete code;
   return LDPC_OK;
 }
@@ -255,14 +310,18 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
   cudaStream_t st = (cudaStream_t)stream;
   const ldpc::DevCode v = view(code);
   cudaError_t err = cudaSuccess;
-  if (ch.kind == Choice::ONCHIP_INT8) {
-    ldpc::IntRule r;
-    r.rule = params->rule;
-    r.beta = params->offset;
-    r.num = params->norm_num;
-    r.shift = params->norm_shift;
-    r.qm = params->msg_sat;
-    const int form = params->form == LDPC_FORM_SS_1BIT ? 1 : 0;
+  ldpc::IntRule r;
+  r.rule = params->rule;
+  r.beta = params->offset;
+  r.num = params->norm_num;
+  r.shift = params->norm_shift;
+  r.qm = params->msg_sat;
+  const int form = params->form == LDPC_FORM_SS_1BIT ? 1 : 0;
+  if (ch.kind == Choice::ONCHIP_H2) {
+    err = ldpc::onchip_h2_launch(v, r, form, ch.onchip, code->sm_count, static_cast<const int8_t*>(llr), n_frames,
+                                 params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
+                                 static_cast<int16_t*>(llr_out), st, false);
+  } else if (ch.kind == Choice::ONCHIP_INT8) {
     err = ldpc::onchip_int8_occupancy(form, code->sm_count, &ch.onchip);
     if (err == cudaSuccess)
       err = ldpc::onchip_int8_launch(v, r, form, ch.onchip, static_cast<const int8_t*>(llr), n_frames,

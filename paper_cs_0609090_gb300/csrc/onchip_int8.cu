@@ -83,10 +83,10 @@ __device__ __forceinline__ int32_t sbyte(uint32_t v, int g) { return (int32_t)(i
 // check: bit g of the result is set when check m is unsatisfied for frame g.
 template <int G>
 __device__ __forceinline__ uint32_t row_parity(const DevCode& c, const uint32_t* __restrict__ Zs, int m) {
-  const int e0 = __ldg(c.rp + m), e1 = __ldg(c.rp + m + 1);
+  const int d = c.deg(m);
   uint32_t par = 0;
-  for (int e = e0; e < e1; ++e) {
-    const int n = __ldg(c.ci + e);
+  for (int j = 0; j < d; ++j) {
+    const int n = c.col(j, m);
     uint32_t w[G / 2];
     load_pairs<G>(Zs, n, w);
 #pragma unroll
@@ -105,8 +105,8 @@ __device__ __forceinline__ uint32_t check_update(const DevCode& c, const IntRule
                                                  const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
                                                  uint2* __restrict__ St, int8_t* __restrict__ Lm) {
   constexpr int P = G / 2;
-  const int e0 = __ldg(c.rp + m);
-  const int d = __ldg(c.rp + m + 1) - e0;
+  const int d = c.deg(m);
+  const int M = c.M;
 
   // previous state: A, B, n~ packed in .x (8/8/8 bits), signs in .y
   uint32_t sa[G], ss[G];
@@ -124,11 +124,11 @@ __device__ __forceinline__ uint32_t check_update(const DevCode& c, const IntRule
   for (int g = 0; g < G; ++g) { k1[g] = 0x7fffffff; k2[g] = 0x7fffffff; neg[g] = 0; }
 
   for (int j = 0; j < d; ++j) {
-    const int n = __ldg(c.ci + e0 + j);
+    const int n = c.col(j, m);
     uint32_t w[P];
     load_pairs<G>(Zs, n, w);
     uint32_t lv = 0;
-    if constexpr (FORM == 0) lv = load_edge<G>(Lm, e0 + j);
+    if constexpr (FORM == 0) lv = load_edge<G>(Lm, j * M + m);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int32_t z = (g & 1) ? hi16(w[g / 2]) : lo16(w[g / 2]);
@@ -162,7 +162,7 @@ __device__ __forceinline__ uint32_t check_update(const DevCode& c, const IntRule
   }
 
   for (int j = 0; j < d; ++j) {
-    const int n = __ldg(c.ci + e0 + j);
+    const int n = c.col(j, m);
     int32_t l[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -175,7 +175,7 @@ __device__ __forceinline__ uint32_t check_update(const DevCode& c, const IntRule
       uint32_t v = 0;
 #pragma unroll
       for (int g = 0; g < G; ++g) v |= ((uint32_t)l[g] & 0xffu) << (8 * g);
-      store_edge<G>(Lm, e0 + j, v);
+      store_edge<G>(Lm, j * M + m, v);
     }
   }
   if constexpr (FORM == 1) {
@@ -202,7 +202,7 @@ onchip_int8_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ 
   constexpr int P = G / 2;
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = c.N, M = c.M;
-  const SmemLayout L = layout(N, M, c.E, G, FORM);
+  const SmemLayout L = layout(N, M, c.ell_w * M, G, FORM);
   uint32_t* Zs = reinterpret_cast<uint32_t*>(smem + L.zs);
   int32_t* Acc = reinterpret_cast<int32_t*>(smem + L.acc);
   uint2* St = reinterpret_cast<uint2*>(smem + L.st);
@@ -232,7 +232,7 @@ onchip_int8_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ 
     if constexpr (FORM == 1) {
       for (int i = tid; i < M * G; i += nt) St[i] = make_uint2(0u, 0u);
     } else {
-      for (int i = tid; i < c.E; i += nt) store_edge<G>(Lm, i, 0u);
+      for (int i = tid; i < c.ell_w * M; i += nt) store_edge<G>(Lm, i, 0u);
     }
     if (tid < 3) s_fail[tid] = 0;
     if (tid < G) s_iters[tid] = max_iter;
@@ -351,13 +351,13 @@ bool onchip_int8_plan(const DevCode& c, int form, int32_t n_frames, int sm_count
   const size_t static_smem = 64;  // s_fail, s_iters, s_ok
   int G = 0;
   for (int g : {4, 2}) {
-    if (layout(c.N, c.M, c.E, g, form).total + static_smem <= smem_optin) { G = g; break; }
+    if (layout(c.N, c.M, c.ell_w * c.M, g, form).total + static_smem <= smem_optin) { G = g; break; }
   }
   if (G == 0) return false;
   // Fewer frames per CTA when that is what it takes to give every SM work.
   while (G > 2 && (int64_t)n_frames < (int64_t)sm_count * G) G /= 2;
   plan->G = G;
-  plan->smem = layout(c.N, c.M, c.E, G, form).total;
+  plan->smem = layout(c.N, c.M, c.ell_w * c.M, G, form).total;
   int threads = ((c.M + 31) / 32) * 32;
   if (threads > kMaxThreads) threads = kMaxThreads;
   if (threads < 128) threads = 128;

@@ -27,6 +27,8 @@ LDPC_RULE_PLAIN, LDPC_RULE_OFFSET, LDPC_RULE_NORMALIZED = 0, 1, 2
 DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_F32}
 FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
 RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED}
+LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF = 0, 1, 2
+KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF}
 
 # Every symbol include/ldpc_gb300.h declares.
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",
@@ -44,7 +46,7 @@ class ldpc_decode_params(ctypes.Structure):
                 ("offset", ctypes.c_int32), ("norm_num", ctypes.c_int32), ("norm_shift", ctypes.c_int32),
                 ("offset_f32", ctypes.c_float), ("norm_f32", ctypes.c_float),
                 ("msg_sat", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("early_stop", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("early_stop", ctypes.c_int32), ("kernel", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -88,7 +90,7 @@ def ldpc_last_error() -> str:
 
 def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=3, norm_shift=2,
                 offset_f32=0.0, norm_f32=0.75, msg_sat=127, max_iter=20, early_stop=1,
-                norm=None, **_ignored) -> ldpc_decode_params:
+                norm=None, kernel="auto", **_ignored) -> ldpc_decode_params:
     """Builds ldpc_decode_params from names ('int8'/'f32', 'ss_fixed'/'ss_1bit'/'two_scan',
     'plain'/'offset'/'normalized').  ``norm`` is an alias for norm_f32."""
     if norm is not None:
@@ -97,7 +99,8 @@ def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=
                               FORMS[form] if isinstance(form, str) else form,
                               RULES[rule] if isinstance(rule, str) else rule,
                               int(offset), int(norm_num), int(norm_shift), float(offset_f32),
-                              float(norm_f32), int(msg_sat), int(max_iter), int(early_stop), 0)
+                              float(norm_f32), int(msg_sat), int(max_iter), int(early_stop),
+                              KERNELS[kernel] if isinstance(kernel, str) else int(kernel))
 
 
 def ldpc_code_create(n_vars: int, n_checks: int, row_ptr, col_idx, device: int = 0) -> int:

@@ -6,6 +6,7 @@ import oracle
 from paper_cs_0609090_gb300 import inputs as I
 
 FORMS_INT = ("ss_1bit", "ss_fixed")
+KERNELS_INT = ("onchip_half", "onchip_int")
 
 
 def gpu_decode(code_handle, n_vars, q0, params, want_llr=True):

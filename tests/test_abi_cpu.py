@@ -37,6 +37,7 @@ def test_library_exports_every_declared_symbol(L):
 def test_params_struct_layout(L):
     # 12 four-byte fields, as in ldpc_decode_params
     assert ctypes.sizeof(L.ldpc_decode_params) == 48
+    assert [f[0] for f in L.ldpc_decode_params._fields_][-1] == "kernel"
 
 
 def _create_raw(L, n_vars, n_checks, rp, ci):

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_cs_0609090_gb300 import inputs as I
-from gpu_helpers import FORMS_INT, assert_int_parity, gpu_decode, oracle_int
+from gpu_helpers import FORMS_INT, KERNELS_INT, assert_int_parity, gpu_decode, oracle_int
 
 pytestmark = pytest.mark.gpu
 
@@ -19,14 +19,15 @@ def L():
     return ldpc
 
 
-def _run(L, code, q0, form, p, frames=None):
+def _run(L, code, q0, form, p, frames=None, kernels=("auto",)):
     h = L.Code.from_inputs(code)
-    params = L.make_params(form=form, **p)
-    g = gpu_decode(h, code.n_vars, q0, params)
     o = oracle_int(code, q0 if frames is None else q0[frames], form, p)
-    if frames is not None:
-        g = {k: v[frames] for k, v in g.items()}
-    assert_int_parity(g, o)
+    for kern in kernels:
+        params = L.make_params(form=form, kernel=kern, **p)
+        g = gpu_decode(h, code.n_vars, q0, params)
+        if frames is not None:
+            g = {k: v[frames] for k, v in g.items()}
+        assert_int_parity(g, o)
     return g
 
 
@@ -51,14 +52,14 @@ def test_hamming_golden(L, form):
 def test_regular_1008_full_batch(L, form, early_stop):
     w = I.make_workload("reg36_n1008")
     p = dict(w.params, early_stop=early_stop)
-    _run(L, w.code, w.q0, form, p)
+    _run(L, w.code, w.q0, form, p, kernels=KERNELS_INT)
 
 
 @pytest.mark.parametrize("form", FORMS_INT)
 @pytest.mark.parametrize("ebn0", [2.0, 2.5, 3.0])
 def test_qc_7493(L, form, ebn0):
     w = I.make_workload("qc_n7493", n_frames=203, ebn0_db=ebn0, frame_seed=int(ebn0 * 10))
-    _run(L, w.code, w.q0, form, w.params)
+    _run(L, w.code, w.q0, form, w.params, kernels=KERNELS_INT)
 
 
 @pytest.mark.parametrize("form", FORMS_INT)
@@ -70,25 +71,26 @@ def test_qc_7493_full_batch_sampled(L, form):
     rng = np.random.default_rng(0)
     frames = np.unique(np.concatenate([rng.choice(w.n_frames, 40, replace=False),
                                        [0, 1, w.n_frames - 2, w.n_frames - 1]]))
-    _run(L, w.code, w.q0, form, p, frames=frames)
+    _run(L, w.code, w.q0, form, p, frames=frames, kernels=KERNELS_INT)
 
 
 @pytest.mark.parametrize("form", FORMS_INT)
 def test_edge_cases(L, form):
     w = I.make_workload("reg36_n1008", n_frames=7, ebn0_db=1.0)
+    K = KERNELS_INT
     # one frame, odd frame count (ragged frame pair), max_iter = 0
-    _run(L, w.code, w.q0[:1], form, w.params)
-    _run(L, w.code, w.q0, form, w.params)
-    _run(L, w.code, w.q0, form, dict(w.params, max_iter=0))
-    _run(L, w.code, w.q0, form, dict(w.params, max_iter=1, early_stop=0))
+    _run(L, w.code, w.q0[:1], form, w.params, kernels=K)
+    _run(L, w.code, w.q0, form, w.params, kernels=K)
+    _run(L, w.code, w.q0, form, dict(w.params, max_iter=0), kernels=K)
+    _run(L, w.code, w.q0, form, dict(w.params, max_iter=1, early_stop=0), kernels=K)
     # noise-free frames stop before the first iteration
     q = I.noiseless(w.codewords, 31)
-    g = _run(L, w.code, q, form, w.params)
+    g = _run(L, w.code, q, form, w.params, kernels=K)
     assert np.all(g["iters"] == 0) and np.all(g["ok"] == 1)
     # extreme channel values, full int8 range
     rng = np.random.default_rng(3)
     q = rng.integers(-128, 128, size=(9, w.code.n_vars)).astype(np.int8)
-    _run(L, w.code, q, form, dict(w.params, msg_sat=127, rule="plain", early_stop=0, max_iter=12))
+    _run(L, w.code, q, form, dict(w.params, msg_sat=127, rule="plain", early_stop=0, max_iter=12), kernels=K)
 
 
 @pytest.mark.parametrize("form", FORMS_INT)
@@ -107,6 +109,11 @@ def test_rules_and_irregular_degrees(L, form, rule):
     p = dict(rule=rule, offset=2, norm_num=3, norm_shift=2, msg_sat=63, max_iter=9, early_stop=1)
     _run(L, code, q0, form, p)
     _run(L, code, q0, form, dict(p, early_stop=0))
+    # the same rules on a code the packed kernel accepts (row degree <= 16)
+    rows16 = [r[:16] for r in rows]
+    code16 = I.from_rows(N, rows16, sort=False)
+    _run(L, code16, q0, form, p, kernels=KERNELS_INT)
+    _run(L, code16, q0, form, dict(p, early_stop=0, rule=rule, norm_num=5, norm_shift=3), kernels=KERNELS_INT)
 
 
 @pytest.mark.parametrize("seed", range(3))
@@ -115,11 +122,24 @@ def test_tree_and_permuted_codes(L, seed):
     rng = np.random.default_rng(seed)
     q0 = rng.integers(-20, 21, size=(33, 18)).astype(np.int8)
     for form in FORMS_INT:
-        _run(L, code, q0, form, dict(rule="plain", msg_sat=127, max_iter=36, early_stop=0))
+        _run(L, code, q0, form, dict(rule="plain", msg_sat=127, max_iter=36, early_stop=0), kernels=KERNELS_INT)
     w = I.make_workload("reg36_n1008", n_frames=64, ebn0_db=1.7)
     pc, _ = I.permuted(w.code, seed=seed)
     for form in FORMS_INT:
-        _run(L, pc, w.q0, form, w.params)
+        _run(L, pc, w.q0, form, w.params, kernels=KERNELS_INT)
+
+
+def test_forced_kernel_rejects_ineligible_code(L):
+    """The packed kernel refuses codes whose magnitudes could reach 2048."""
+    rng = np.random.default_rng(1)
+    rows = [rng.choice(200, size=20, replace=False) for _ in range(40)]   # degree 20 > 16
+    code = I.from_rows(200, rows, sort=False)
+    h = L.Code.from_inputs(code)
+    import torch
+    q = torch.zeros((2, 200), dtype=torch.int8, device="cuda")
+    with pytest.raises(L.LdpcError) as e:
+        L.decode(h, q, L.make_params(kernel="onchip_half", max_iter=3))
+    assert e.value.status == L.LDPC_ERR_UNSUPPORTED
 
 
 def test_unsupported_code_reports_cleanly(L):
