@@ -38,24 +38,27 @@ METRIC = "decoded info Gbit/s at fixed iters, single-scan vs two-scan; FER @ sta
 UNIT = "Gbit/s"
 
 
-def algorithmic_bytes(code, form: str, iters: int, frames: int) -> dict:
+def algorithmic_bytes(code, form: str, iters: int, frames: int, dtype: str = "int8") -> dict:
     """Streaming-model bytes of one decode: per frame-iteration 2 b_z N + 2 S_L
     (read and write of the posterior and of the message state) plus per frame
-    the int8 LLRs in, packed decisions out and 5 bytes of iteration count/flag."""
+    the LLRs in, packed decisions out and 5 bytes of iteration count/flag.
+    int8: b_z = 2, S_L = (ceil(d_c/8) + 3) M (Section V) or E (per edge);
+    float32: b_z = 4, S_L = (ceil(d_c/8) + 9) M or 4 E."""
     N, M, E = code.n_vars, code.n_checks, code.n_edges
     dmax = int(code.row_degrees().max())
-    b_z = 2
+    f32 = dtype == "f32"
+    b_z = 4 if f32 else 2
     if form == "ss_1bit":
-        s_l = ((dmax + 7) // 8 + 3) * M
+        s_l = ((dmax + 7) // 8 + (9 if f32 else 3)) * M
     elif form == "ss_fixed":
-        s_l = E
+        s_l = (4 if f32 else 1) * E
     else:  # two-scan: Z_mn and L_mn cells read and written, plus q0 and decisions
         s_l = None
     if s_l is None:
-        b_it = 4 * E + N + N // 8
+        b_it = (4 if not f32 else 16) * E + N + N // 8
     else:
         b_it = 2 * b_z * N + 2 * s_l
-    b_io = N + (N + 7) // 8 + 5
+    b_io = N * (4 if f32 else 1) + (N + 7) // 8 + 5
     return dict(per_frame_iter=b_it, per_frame_io=b_io, per_launch=frames * (iters * b_it + b_io))
 
 
@@ -204,7 +207,8 @@ def main():
     ap.add_argument("--workload", default="qc_n7493")
     ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half", "stream"])
+    ap.add_argument("--dtype", default="int8", choices=["int8", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -221,18 +225,24 @@ def main():
     w.params["early_stop"] = 0
     F, N, K = w.n_frames, w.code.n_vars, w.K
     code = ldpc.Code.from_inputs(w.code, device=local)
-    params = ldpc.make_params(form=args.form, kernel=args.kernel, **w.params)
+    wp = dict(w.params)
+    if args.dtype == "f32":
+        wp["dtype"] = "f32"
+    params = ldpc.make_params(form=args.form, kernel=args.kernel, **wp)
+    ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
     kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel"}.get(args.kernel)
-    if kname is None:
+    if ws_bytes > 0:
+        kname = "f32s_rows" if args.dtype == "f32" else "h2s_rows"
+    elif kname is None:
         info = ldpc.ldpc_code_info(code.handle)
         half_ok = info["max_row_degree"] <= 16 and \
             128 + (info["max_col_degree"] + 1) * w.params["msg_sat"] <= 2048
         kname = "onchip_h2_kernel" if half_ok else "onchip_int8_kernel"
-    llr = torch.from_numpy(w.q0).to(dev)
+    host_llr = w.q0 if args.dtype == "int8" else w.llr.astype(np.float32)
+    llr = torch.from_numpy(host_llr).to(dev)
     bits = torch.empty((F, (N + 7) // 8), dtype=torch.uint8, device=dev)
     iters = torch.empty(F, dtype=torch.int32, device=dev)
     ok = torch.empty(F, dtype=torch.uint8, device=dev)
-    ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
     ws = torch.empty(max(ws_bytes, 1) + 256, dtype=torch.uint8, device=dev)
     ws_ptr = (ws.data_ptr() + 255) & ~255
     stream = torch.cuda.Stream(device=dev)
@@ -250,7 +260,7 @@ def main():
         for _ in range(args.warmup):
             step()
     torch.cuda.synchronize()
-    # sanity: all frames ran the fixed iteration count
+    # all frames ran the fixed iteration count
     assert int(iters.min()) == w.params["max_iter"] and int(iters.max()) == w.params["max_iter"]
 
     if world > 1:
@@ -272,7 +282,7 @@ def main():
     total_ms = float(np.sum(dev_ms))
 
     # end to end through the C ABI: pinned host LLRs in, decisions/iters/flags out
-    h_llr = torch.from_numpy(w.q0).pin_memory()
+    h_llr = torch.from_numpy(host_llr).pin_memory()
     h_bits = torch.empty_like(bits, device="cpu").pin_memory()
     h_iters = torch.empty_like(iters, device="cpu").pin_memory()
     h_ok = torch.empty_like(ok, device="cpu").pin_memory()
@@ -305,7 +315,7 @@ def main():
     ms_step = total_ms / args.steps
     value = world * F * K / (ms_step * 1e-3) / 1e9
     e2e_val = world * F * K / (e2e_ms / args.steps * 1e-3) / 1e9
-    ab = algorithmic_bytes(w.code, args.form, w.params["max_iter"], F)
+    ab = algorithmic_bytes(w.code, args.form, w.params["max_iter"], F, args.dtype)
     peaks = measured_peaks()
     achieved = ab["per_launch"] / (ms_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -316,17 +326,17 @@ def main():
                 "kernel": kname, "kernel_ms": ms_step}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": w.name, "form": args.form, "n_frames": F, "iters": w.params["max_iter"],
                        "N": N, "M": w.code.n_checks, "E": w.code.n_edges, "K": K,
                        "ebn0_db": w.ebn0_db, "rule": w.params["rule"], "early_stop": 0,
                        "l2": "flushed between timed steps (256 MB write)", "frames_per_rank": F,
                        "kernel": args.kernel},
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(w.q0.nbytes),
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(host_llr.nbytes),
                     "d2h_bytes_per_step": int(bits.numel() + iters.numel() * 4 + ok.numel())},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (1 if ws_bytes == 0 else 3 + 2 * w.params["max_iter"]),
             "roofline": roofline, "clocks": clocks}
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.dtype == "int8":
         info, _ = cpu_oracle_sample(w, args.form, budget_s=float(os.environ.get("BENCH_CPU_BUDGET_S", "12")),
                                     max_frames=F)
         line["cpu_baseline"] = info

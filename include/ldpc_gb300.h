@@ -85,6 +85,9 @@ enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2 };
  *                                         degree <= 16 and
  *                                         128 + (max_col_degree + 1) * msg_sat <= 2048
  *                                         and n_vars <= 65535)
+ *                LDPC_KERNEL_STREAM       frame state in device memory (the
+ *                                         workspace); for codes too large for one
+ *                                         SM; the only kernel of the float32 path
  */
 typedef struct {
   int32_t dtype;
@@ -101,7 +104,7 @@ typedef struct {
   int32_t kernel;
 } ldpc_decode_params;
 
-enum { LDPC_KERNEL_AUTO = 0, LDPC_KERNEL_ONCHIP_INT = 1, LDPC_KERNEL_ONCHIP_HALF = 2 };
+enum { LDPC_KERNEL_AUTO = 0, LDPC_KERNEL_ONCHIP_INT = 1, LDPC_KERNEL_ONCHIP_HALF = 2, LDPC_KERNEL_STREAM = 3 };
 
 /* Build a code from the check->variable adjacency N(m) of H (Section II).
  *   row_ptr  host, [n_checks + 1], row_ptr[0] = 0, non-decreasing.

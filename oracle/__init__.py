@@ -71,6 +71,9 @@ def _load():
         _lib.orc_decode_f64.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P, P,
                                         ctypes.c_int32]
         _lib.orc_decode_f64.restype = ctypes.c_int
+        _lib.orc_decode_f64_margin.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P, P, P,
+                                               ctypes.c_int32]
+        _lib.orc_decode_f64_margin.restype = ctypes.c_int
         _lib.orc_default_threads.restype = ctypes.c_int32
     return _lib
 
@@ -129,9 +132,12 @@ def decode_int(code, q0, *, form="ss_1bit", rule="plain", offset=0, norm_num=3, 
 
 
 def decode_f64(code, q0, *, form="ss_1bit", rule="normalized", offset=0.0, lam=0.75,
-               max_iter=50, early_stop=1, beta_tab=None, want_l=False, threads=0) -> Result:
+               max_iter=50, early_stop=1, beta_tab=None, want_l=False, want_margin=False,
+               threads=0) -> Result:
     """Double-precision min-sum decode of q0 (float [F, N]).  ``beta_tab``:
-    optional [max_iter, M] per-iteration, per-check offsets (rule must be 'offset')."""
+    optional [max_iter, M] per-iteration, per-check offsets (rule must be 'offset').
+    ``want_margin`` adds ``margin`` [F]: the frame's smallest |Z^(k)_n| over all
+    iterations, its distance to the decision rule."""
     lib = _load()
     q = np.ascontiguousarray(np.atleast_2d(q0), dtype=np.float64)
     F, N = q.shape
@@ -149,11 +155,14 @@ def decode_f64(code, q0, *, form="ss_1bit", rule="normalized", offset=0.0, lam=0
     ok = np.zeros(F, np.uint8)
     z = np.zeros((F, N), np.float64)
     l_out = np.zeros((F, E), np.float64) if want_l else None
-    rc = lib.orc_decode_f64(ctypes.byref(c), ctypes.byref(p), FORMS[form], _ptr(q), F, _ptr(bits),
-                            _ptr(iters), _ptr(ok), _ptr(z), _ptr(l_out), int(threads))
+    mg = np.zeros(F, np.float64) if want_margin else None
+    rc = lib.orc_decode_f64_margin(ctypes.byref(c), ctypes.byref(p), FORMS[form], _ptr(q), F, _ptr(bits),
+                                   _ptr(iters), _ptr(ok), _ptr(z), _ptr(l_out), _ptr(mg), int(threads))
     if rc != 0:
         raise ValueError("orc_decode_f64 rejected its arguments")
     r = Result(bits=bits, iters=iters, ok=ok, z=z)
     if want_l:
         r["l"] = l_out
+    if want_margin:
+        r["margin"] = mg
     return r

@@ -242,7 +242,9 @@ typedef struct {
 
 static void decode_frame_f64(const orc_code *c, const orc_csc *t, const orc_dparams *p,
                              int32_t form, const double *q0, dscratch *w, uint8_t *bits,
-                             int32_t *iters, uint8_t *ok, double *z_out, double *l_out) {
+                             int32_t *iters, uint8_t *ok, double *z_out, double *l_out,
+                             double *margin) {
+  double mg = INFINITY;
   const int32_t N = c->n_vars, M = c->n_checks, E = c->row_ptr[M];
   const int32_t *rp = c->row_ptr, *ci = c->col_idx;
   double *Z = w->Z, *Zprev = w->Zprev, *L = w->L;
@@ -253,6 +255,7 @@ static void decode_frame_f64(const orc_code *c, const orc_csc *t, const orc_dpar
 
   int32_t k = 0;
   int sat = decide_and_check(c, NULL, Z, w->x);
+  for (int32_t n = 0; n < N; ++n) if (fabs(Z[n]) < mg) mg = fabs(Z[n]);
   if (!(p->early_stop && sat)) {
     for (k = 1; k <= p->max_iter; ++k) {
       memcpy(Zprev, Z, sizeof(double) * (size_t)N);
@@ -319,6 +322,7 @@ static void decode_frame_f64(const orc_code *c, const orc_csc *t, const orc_dpar
         }
       }
       sat = decide_and_check(c, NULL, Z, w->x);
+      for (int32_t n = 0; n < N; ++n) if (fabs(Z[n]) < mg) mg = fabs(Z[n]);
       if (p->early_stop && sat) break;
     }
     if (k > p->max_iter) k = p->max_iter;
@@ -328,6 +332,7 @@ static void decode_frame_f64(const orc_code *c, const orc_csc *t, const orc_dpar
   for (int32_t n = 0; n < N; ++n) { bits[n] = w->x[n]; z_out[n] = Z[n]; }
   if (l_out)
     for (int32_t e = 0; e < E; ++e) l_out[e] = L[e];
+  if (margin) *margin = mg;
 }
 
 /* ------------------------------------------------------------ threading */
@@ -346,6 +351,7 @@ typedef struct {
   uint8_t *ok;
   void *z_out, *l_out;
   int32_t *state_out;
+  double *margin_out;
   int err;
 } job;
 
@@ -394,7 +400,8 @@ static void *run_job(void *arg) {
       for (int32_t f = jb->f0; f < jb->f1; ++f)
         decode_frame_f64(c, jb->t, jb->dp, jb->form, q0 + (size_t)f * N, &w, jb->bits + (size_t)f * N,
                          jb->iters + f, jb->ok + f, (double *)jb->z_out + (size_t)f * N,
-                         jb->l_out ? (double *)jb->l_out + (size_t)f * E : NULL);
+                         jb->l_out ? (double *)jb->l_out + (size_t)f * E : NULL,
+                         jb->margin_out ? jb->margin_out + f : NULL);
     }
     free(w.Z); free(w.Zprev); free(w.L); free(w.Zmn); free(w.u); free(w.Lraw);
     free(w.A); free(w.B); free(w.nt); free(w.s); free(w.x);
@@ -462,6 +469,12 @@ int orc_decode_int(const orc_code *code, const orc_iparams *p, int32_t form, con
 int orc_decode_f64(const orc_code *code, const orc_dparams *p, int32_t form, const double *q0,
                    int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok, double *z_out,
                    double *l_out, int32_t n_threads) {
+  return orc_decode_f64_margin(code, p, form, q0, n_frames, bits, iters, ok, z_out, l_out, NULL, n_threads);
+}
+
+int orc_decode_f64_margin(const orc_code *code, const orc_dparams *p, int32_t form, const double *q0,
+                          int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok, double *z_out,
+                          double *l_out, double *margin_out, int32_t n_threads) {
   if (validate(code, form) || !p || p->max_iter < 0 || n_frames < 0) return -1;
   if (n_frames == 0) return 0;
   if (!q0 || !bits || !iters || !ok || !z_out) return -1;
@@ -469,5 +482,6 @@ int orc_decode_f64(const orc_code *code, const orc_dparams *p, int32_t form, con
   memset(&proto, 0, sizeof proto);
   proto.c = code; proto.form = form; proto.is_int = 0; proto.dp = p; proto.q0 = q0;
   proto.bits = bits; proto.iters = iters; proto.ok = ok; proto.z_out = z_out; proto.l_out = l_out;
+  proto.margin_out = margin_out;
   return run_all(&proto, n_frames, n_threads);
 }

@@ -78,9 +78,19 @@ int orc_decode_int(const orc_code *code, const orc_iparams *p, int32_t form,
                    uint8_t *ok, int32_t *z_out, int32_t *l_out, int32_t *state_out,
                    int32_t n_threads);
 
+/* margin_out [F] (nullable): the smallest |Z^(k)_n| over every iteration k
+   (including k = 0) and variable n -- the distance to the decision rule, the
+   only discontinuity of min-sum decoding (the check rule, offset, scaling and
+   sums are Lipschitz in their inputs).  Frames with a small margin are those
+   whose decisions or stopping iteration a different rounding may change; it is
+   a diagnostic and does not affect decoding. */
 int orc_decode_f64(const orc_code *code, const orc_dparams *p, int32_t form,
                    const double *q0, int32_t n_frames, uint8_t *bits, int32_t *iters,
                    uint8_t *ok, double *z_out, double *l_out, int32_t n_threads);
+int orc_decode_f64_margin(const orc_code *code, const orc_dparams *p, int32_t form,
+                          const double *q0, int32_t n_frames, uint8_t *bits, int32_t *iters,
+                          uint8_t *ok, double *z_out, double *l_out, double *margin_out,
+                          int32_t n_threads);
 
 /* Number of threads orc_decode_* would use for n_threads <= 0. */
 int32_t orc_default_threads(void);

@@ -43,4 +43,19 @@ cudaError_t onchip_h2_launch(const DevCode& c, const IntRule& r, int form, Onchi
                              const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
                              int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t stream, bool occupancy_only);
 
+// Device-memory (streaming) decoders for codes whose frame state does not fit
+// one SM.  All state lives in the caller's workspace (layout below).
+struct StreamLayout {
+  int lanes = 0;  // frame pairs (int8) or frames (float32), padded to 32
+  size_t z = 0, acc = 0, st = 0, q0 = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
+};
+StreamLayout stream_layout(int dtype, int form, int N, int M, int E, int F);
+bool stream_int8_eligible(int max_row_deg, int max_col_deg, int qm);
+cudaError_t stream_int8_decode(const DevCode& c, const IntRule& r, int form, const StreamLayout& L, void* ws,
+                               int sm_count, const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop,
+                               uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st);
+cudaError_t stream_f32_decode(const DevCode& c, const F32Rule& r, int form, const StreamLayout& L, void* ws,
+                              int sm_count, const float* llr, int32_t F, int32_t max_iter, int32_t early_stop,
+                              uint8_t* bits, int32_t* iters, uint8_t* ok, float* zout, cudaStream_t st);
+
 }  // namespace ldpc

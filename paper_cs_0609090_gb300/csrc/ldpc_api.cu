@@ -84,7 +84,7 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   if (p->max_iter < 0) return fail(LDPC_ERR_INVALID_ARG, "max_iter %d < 0", p->max_iter);
   if (p->early_stop != 0 && p->early_stop != 1)
     return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");
-  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_ONCHIP_HALF)
+  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_STREAM)
     return fail(LDPC_ERR_INVALID_ARG, "kernel %d is not a known LDPC_KERNEL_*", p->kernel);
   if (p->dtype == LDPC_DTYPE_INT8) {
     if (p->msg_sat < 1 || p->msg_sat > 127)
@@ -111,8 +111,9 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
 
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
-  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2 } kind = NONE;
+  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, STREAM_INT8, STREAM_F32 } kind = NONE;
   ldpc::OnchipPlan onchip;
+  ldpc::StreamLayout stream;
   size_t ws = 0;
 };
 
@@ -122,6 +123,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     const int form = p->form == LDPC_FORM_SS_1BIT ? 1 : 0;
     const bool want_half = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF;
     const bool want_int = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_INT;
+    const bool want_stream = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM;
     if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat) &&
         ldpc::onchip_h2_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_H2;
@@ -133,11 +135,25 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
       ch->ws = 0;
       return LDPC_OK;
     }
+    if (want_stream && ldpc::stream_int8_eligible(c->max_row_deg, c->max_col_deg, p->msg_sat)) {
+      ch->kind = Choice::STREAM_INT8;
+      ch->stream = ldpc::stream_layout(0, form, c->N, c->M, c->E, n_frames);
+      ch->ws = ch->stream.total;
+      return LDPC_OK;
+    }
     return fail(LDPC_ERR_UNSUPPORTED, "code (N=%d, M=%d, E=%d, row degree <= %d, column degree <= %d) "
                 "cannot run on the requested frame-resident kernel (%d)",
                 c->N, c->M, c->E, c->max_row_deg, c->max_col_deg, p->kernel);
   }
-  return fail(LDPC_ERR_UNSUPPORTED, "dtype %d / form %d is not available in this build", p->dtype, p->form);
+  if (p->dtype == LDPC_DTYPE_F32 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED) &&
+      (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM)) {
+    ch->kind = Choice::STREAM_F32;
+    ch->stream = ldpc::stream_layout(1, p->form == LDPC_FORM_SS_1BIT ? 1 : 0, c->N, c->M, c->E, n_frames);
+    ch->ws = ch->stream.total;
+    return LDPC_OK;
+  }
+  return fail(LDPC_ERR_UNSUPPORTED, "dtype %d / form %d / kernel %d is not available in this build", p->dtype,
+              p->form, p->kernel);
 }
 
 }  // namespace
@@ -321,6 +337,18 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
     err = ldpc::onchip_h2_launch(v, r, form, ch.onchip, code->sm_count, static_cast<const int8_t*>(llr), n_frames,
                                  params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
                                  static_cast<int16_t*>(llr_out), st, false);
+  } else if (ch.kind == Choice::STREAM_INT8) {
+    err = ldpc::stream_int8_decode(v, r, form, ch.stream, workspace, code->sm_count, static_cast<const int8_t*>(llr),
+                                   n_frames, params->max_iter, params->early_stop, hard_bits, iters_used,
+                                   syndrome_ok, static_cast<int16_t*>(llr_out), st);
+  } else if (ch.kind == Choice::STREAM_F32) {
+    ldpc::F32Rule fr;
+    fr.rule = params->rule;
+    fr.beta = params->offset_f32;
+    fr.lambda = params->norm_f32;
+    err = ldpc::stream_f32_decode(v, fr, form, ch.stream, workspace, code->sm_count, static_cast<const float*>(llr),
+                                  n_frames, params->max_iter, params->early_stop, hard_bits, iters_used,
+                                  syndrome_ok, static_cast<float*>(llr_out), st);
   } else if (ch.kind == Choice::ONCHIP_INT8) {
     err = ldpc::onchip_int8_occupancy(form, code->sm_count, &ch.onchip);
     if (err == cudaSuccess)

@@ -1,0 +1,597 @@
+// stream.cu -- single-scan min-sum with frame state in device memory, for codes
+// whose per-frame state does not fit one SM (Section IV Eq. (3), Section V).
+//
+// Workspace layout (frame-pair or frame index innermost, so that the lanes of a
+// warp -- consecutive frames -- read and atomically update consecutive words):
+//   int8 path, lane = frame pair, exact binary16 arithmetic (see h2ops.cuh):
+//     Zs [N][FP] half2, Acc [N][FP] i32 (lo + 65536 hi, biased like onchip_h2),
+//     state [M][FP] uint4 (Section V) or [E][FP] u16 (per-edge bytes L + 128),
+//     q0 [N][FP] u16 (int8 pair), act/fail [2][FP] u32 bit masks, iters [2 FP]
+//   float path, lane = frame:
+//     Z [N][FL] f32, Acc [N][FL] f32, state [M][FL] uint4 {A, B, n~, signs} or
+//     [E][FL] f32, q0 [N][FL] f32, act/fail [2][FL] u32, iters [FL]
+// Per iteration: a row kernel (one warp = one check for 32 lanes of frames; the
+// check's column indices are warp-uniform loads) then a column kernel that
+// applies the stop rule and resets the accumulator.  The syndrome of x^(k-1) is
+// computed by the row kernel of iteration k.  The float accumulation uses
+// floating-point atomics, so its rounding depends on the order of the additions.
+#include <algorithm>
+
+#include "h2ops.cuh"
+#include "kernels.h"
+
+namespace ldpc {
+namespace {
+
+constexpr int kRowsPerWarp = 4;
+constexpr int kWarpsPerBlock = 8;
+
+__host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+StreamLayout stream_layout(int dtype, int form, int N, int M, int E, int F) {
+  StreamLayout L;
+  const bool f32 = dtype == 1;
+  const size_t lanes = f32 ? (size_t)((F + 31) / 32) * 32 : (size_t)(((F + 1) / 2 + 31) / 32) * 32;
+  L.lanes = (int)lanes;
+  size_t off = 0;
+  L.z = off;     off = al256(off + (size_t)N * lanes * 4);
+  L.acc = off;   off = al256(off + (size_t)N * lanes * 4);
+  L.st = off;
+  if (form == 1) off = al256(off + (size_t)M * lanes * 16);
+  else off = al256(off + (size_t)E * lanes * (f32 ? 4 : 2));
+  L.q0 = off;    off = al256(off + (size_t)N * lanes * (f32 ? 4 : 2));
+  L.act = off;   off = al256(off + 2 * lanes * 4);
+  L.fail = off;  off = al256(off + 2 * lanes * 4);
+  L.iters = off; off = al256(off + 2 * lanes * 4);
+  L.ok = off;    off = al256(off + 2 * lanes * 4);
+  L.total = off;
+  return L;
+}
+
+bool stream_int8_eligible(int max_row_deg, int max_col_deg, int qm) {
+  return max_row_deg <= 16 && 128 + (int64_t)max_col_deg * qm + qm <= 2048;
+}
+
+namespace {
+
+// ------------------------------------------------------------------ int8, packed
+
+struct H2S {
+  uint32_t* z;
+  int32_t* acc;
+  uint4* st;
+  uint16_t* lm;
+  uint16_t* q0;
+  uint32_t* act;   // [2][FP]
+  uint32_t* fail;  // [2][FP]
+  int32_t* iters;  // [2 FP]: frame 2p + b
+  uint32_t* ok;    // [FP]
+  int FP;
+};
+
+H2S h2s_view(void* ws, const StreamLayout& L) {
+  char* b = static_cast<char*>(ws);
+  H2S s;
+  s.z = reinterpret_cast<uint32_t*>(b + L.z);
+  s.acc = reinterpret_cast<int32_t*>(b + L.acc);
+  s.st = reinterpret_cast<uint4*>(b + L.st);
+  s.lm = reinterpret_cast<uint16_t*>(b + L.st);
+  s.q0 = reinterpret_cast<uint16_t*>(b + L.q0);
+  s.act = reinterpret_cast<uint32_t*>(b + L.act);
+  s.fail = reinterpret_cast<uint32_t*>(b + L.fail);
+  s.iters = reinterpret_cast<int32_t*>(b + L.iters);
+  s.ok = reinterpret_cast<uint32_t*>(b + L.ok);
+  s.FP = L.lanes;
+  return s;
+}
+
+// Transposes the frame-major int8 LLRs into pair-interleaved order and sets
+// Z^(0), the biased accumulator and the per-pair flags.  Tile: 64 variables x
+// 32 pairs (64 frames).
+__global__ void __launch_bounds__(256) h2s_init(const DevCode c, const int8_t* __restrict__ llr, int32_t F,
+                                                int32_t max_iter, H2S s) {
+  __shared__ int8_t tile[64][65];  // [frame][variable]
+  const int n0 = blockIdx.x * 64, p0 = blockIdx.y * 32;
+  const int N = c.N;
+  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+    const int fl = i >> 6, nl = i & 63;
+    const int f = 2 * p0 + fl, n = n0 + nl;
+    tile[fl][nl] = (f < F && n < N) ? llr[(size_t)f * N + n] : (int8_t)0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+    const int nl = i >> 5, pl = i & 31;
+    const int n = n0 + nl, p = p0 + pl;
+    if (n >= N) continue;
+    const int32_t lo = tile[2 * pl][nl], hi = tile[2 * pl + 1][nl];
+    const size_t o = (size_t)n * s.FP + p;
+    s.q0[o] = (uint16_t)(((uint32_t)lo & 0xffu) | (((uint32_t)hi & 0xffu) << 8));
+    s.z[o] = ints_to_h2(lo, hi);
+    s.acc[o] = (int32_t)((uint32_t)acc_pack(lo, hi) - (uint32_t)__ldg(c.cdeg + n) * 0x66006600u);
+  }
+  if (blockIdx.x == 0) {
+    for (int pl = threadIdx.x; pl < 32; pl += blockDim.x) {
+      const int p = p0 + pl;
+      const uint32_t valid = (2 * p < F ? 1u : 0u) | (2 * p + 1 < F ? 2u : 0u);
+      s.act[s.FP + p] = valid;  // read at k = 1 (odd)
+      s.act[p] = 0u;
+      s.fail[p] = 0u;
+      s.fail[s.FP + p] = 0u;
+      s.iters[2 * p] = max_iter;
+      s.iters[2 * p + 1] = max_iter;
+      s.ok[p] = 0u;
+    }
+  }
+}
+
+// One check for the frame pair of this lane (Eq. (3); Section V state or
+// per-edge bytes).  Returns the decision parity of x^(k-1) (bit 0 lo, bit 1 hi).
+template <int FORM, bool ES>
+__device__ __forceinline__ uint32_t h2s_check(const DevCode& c, const IntRule& r, uint32_t qm2, int m, int p,
+                                              const H2S& s) {
+  const size_t FP = (size_t)s.FP;
+  const int e0 = __ldg(c.rp + m);
+  const int d = __ldg(c.rp + m + 1) - e0;
+  uint32_t A2 = 0, B2 = 0, I2 = 0, S = 0;
+  if constexpr (FORM == 1) {
+    const uint4 st = s.st[(size_t)m * FP + p];
+    A2 = st.x;
+    B2 = st.y;
+    I2 = st.z;
+    S = st.w;
+  }
+  uint32_t K1 = h2c(2048), K2 = h2c(2048), X = 0, NEG = 0, Y = 0;
+  uint32_t jj = 0;  // position j as half2
+  for (int j = 0; j < d; ++j, jj = hadd(jj, h2c(1))) {
+    const int n = __ldg(c.ci + e0 + j);
+    const uint32_t w = s.z[(size_t)n * FP + p];
+    uint32_t L;
+    if constexpr (FORM == 1) {
+      // f(A, B, n, n~) with the sign s_mn applied to the binary16 sign bit
+      const uint32_t msk = heq_mask(I2, jj);
+      L = ((B2 & msk) | (A2 & ~msk)) ^ ((S << (15 - j)) & 0x80008000u);
+    } else {
+      const uint32_t b = s.lm[(size_t)(e0 + j) * FP + p];
+      L = hfma(__byte_perm(b, 0x58u, 0x4140), h2c(8), 0xE480E480u);
+    }
+    const uint32_t u = hsub(w, L);
+    X ^= u;
+    if constexpr (ES) Y ^= dec_bits(w);
+    NEG |= (u & 0x80008000u) >> (15 - j);
+    const uint32_t key = hfma(hmin(habs(u), qm2), h2c(16), jj);
+    K2 = hmin(K2, hmax(K1, key));
+    K1 = hmin(K1, key);
+  }
+  const uint32_t dm = (d >= 16) ? 0xffffu : ((1u << d) - 1u);
+  const uint32_t Sn = (NEG ^ prmt(X, 0u, 0xBB99u)) & (dm | (dm << 16));
+  const int32_t k1l = h_lo_int(K1), k1h = h_hi_int(K1), k2l = h_lo_int(K2), k2h = h_hi_int(K2);
+  const uint32_t An = small_to_h2(r.g(k1l >> 4), r.g(k1h >> 4));
+  const uint32_t Bn = small_to_h2(r.g(k2l >> 4), r.g(k2h >> 4));
+  const uint32_t In = small_to_h2(k1l & 15, k1h & 15);
+  jj = 0;
+  for (int j = 0; j < d; ++j, jj = hadd(jj, h2c(1))) {
+    const int n = __ldg(c.ci + e0 + j);
+    const uint32_t msk = heq_mask(In, jj);
+    const uint32_t mag = (Bn & msk) | (An & ~msk);
+    const uint32_t L = mag ^ ((Sn << (15 - j)) & 0x80008000u);
+    atomicAdd(s.acc + (size_t)n * FP + p, (int32_t)hadd(L, h2c(1536)));
+    if constexpr (FORM == 0) {
+      const uint32_t hb = hfma(L, 0x30003000u, h2c(144));
+      s.lm[(size_t)(e0 + j) * FP + p] = (uint16_t)__byte_perm(hb, 0u, 0x4420);
+    }
+  }
+  if constexpr (FORM == 1) s.st[(size_t)m * FP + p] = make_uint4(An, Bn, In, Sn);
+  return ES ? (((Y >> 15) & 1u) | ((Y >> 30) & 2u)) : 0u;
+}
+
+template <int FORM, bool ES>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) h2s_rows(const DevCode c, const IntRule r, H2S s, int k) {
+  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = s.FP / 32;
+  const int chunk = warp % n_chunks;
+  const int m0 = (warp / n_chunks) * kRowsPerWarp;
+  if (m0 >= c.M) return;
+  const int p = chunk * 32 + lane;
+  const int cur = k & 1;
+  if (__all_sync(0xffffffffu, s.act[cur * s.FP + p] == 0u)) return;
+  const uint32_t qm2 = ints_to_h2(r.qm, r.qm);
+  uint32_t fail = 0;
+  const int m1 = min(m0 + kRowsPerWarp, c.M);
+  for (int m = m0; m < m1; ++m) fail |= h2s_check<FORM, ES>(c, r, qm2, m, p, s);
+  if (ES && fail) atomicOr(s.fail + cur * s.FP + p, fail);
+}
+
+// Stop rule and accumulator reset for every (variable, pair); pair-level flags
+// are advanced by the threads of variable 0.
+template <bool ES>
+__global__ void __launch_bounds__(256) h2s_cols(const DevCode c, H2S s, int k) {
+  const int p = blockIdx.y * 32 + (threadIdx.x & 31);
+  const int cur = k & 1, nxt = cur ^ 1;
+  const uint32_t act = s.act[cur * s.FP + p];
+  const uint32_t stop = ES ? (act & ~s.fail[cur * s.FP + p]) : 0u;
+  const uint32_t cont = act & ~stop;
+  const uint32_t sel = ((cont & 1u) ? 0x0000ffffu : 0u) | ((cont & 2u) ? 0xffff0000u : 0u);
+  for (int n = blockIdx.x * 8 + (threadIdx.x >> 5); n < c.N; n += gridDim.x * 8) {
+    const size_t o = (size_t)n * s.FP + p;
+    const uint32_t zz = acc_to_pair(s.acc[o]);
+    const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
+    s.z[o] = (h & sel) | (s.z[o] & ~sel);
+    const uint32_t q = s.q0[o];
+    s.acc[o] = (int32_t)((uint32_t)acc_pack((int32_t)(int8_t)(q & 0xffu), (int32_t)(int8_t)(q >> 8)) -
+                         (uint32_t)__ldg(c.cdeg + n) * 0x66006600u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    s.act[nxt * s.FP + p] = cont;
+    s.fail[nxt * s.FP + p] = 0u;
+    if (ES) {
+      if (stop & 1u) s.iters[2 * p] = k - 1;
+      if (stop & 2u) s.iters[2 * p + 1] = k - 1;
+      s.ok[p] |= stop;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) h2s_final_syndrome(const DevCode c, H2S s, int kf) {
+  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = s.FP / 32;
+  const int chunk = warp % n_chunks;
+  const int m0 = (warp / n_chunks) * kRowsPerWarp;
+  if (m0 >= c.M) return;
+  const int p = chunk * 32 + lane;
+  const int cur = kf & 1;
+  if (__all_sync(0xffffffffu, s.act[cur * s.FP + p] == 0u)) return;
+  uint32_t fail = 0;
+  const int m1 = min(m0 + kRowsPerWarp, c.M);
+  for (int m = m0; m < m1; ++m) {
+    uint32_t y = 0;
+    for (int e = __ldg(c.rp + m); e < __ldg(c.rp + m + 1); ++e)
+      y ^= dec_bits(s.z[(size_t)__ldg(c.ci + e) * s.FP + p]);
+    fail |= ((y >> 15) & 1u) | ((y >> 30) & 2u);
+  }
+  if (fail) atomicOr(s.fail + cur * s.FP + p, fail);
+}
+
+// Frame-major outputs through a 64-variable x 32-pair tile.
+__global__ void __launch_bounds__(256) h2s_output(const DevCode c, H2S s, int kf, int32_t F, uint8_t* bits,
+                                                  int32_t* iters, uint8_t* okf, int16_t* zout) {
+  __shared__ uint32_t tile[64][33];  // [variable][pair]
+  const int n0 = blockIdx.x * 64, p0 = blockIdx.y * 32;
+  const int N = c.N, N8 = (N + 7) >> 3;
+  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+    const int nl = i >> 5, pl = i & 31;
+    const int n = n0 + nl;
+    tile[nl][pl] = n < N ? s.z[(size_t)n * s.FP + p0 + pl] : 0u;
+  }
+  __syncthreads();
+  // decisions: 8 bytes (64 variables) per frame
+  for (int i = threadIdx.x; i < 64 * 8; i += blockDim.x) {
+    const int fl = i >> 3, bl = i & 7;
+    const int f = 2 * p0 + fl, b = (n0 >> 3) + bl;
+    if (f >= F || b >= N8) continue;
+    uint32_t byte = 0;
+    for (int t = 0; t < 8; ++t) {
+      const int nl = bl * 8 + t;
+      if (n0 + nl < N) byte |= ((dec_bits(tile[nl][fl >> 1] >> (16 * (fl & 1))) >> 15) & 1u) << t;
+    }
+    bits[(size_t)f * N8 + b] = (uint8_t)byte;
+  }
+  if (zout != nullptr) {
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+      const int fl = i >> 6, nl = i & 63;
+      const int f = 2 * p0 + fl, n = n0 + nl;
+      if (f >= F || n >= N) continue;
+      const uint32_t h = tile[nl][fl >> 1];
+      zout[(size_t)f * N + n] = (int16_t)((fl & 1) ? h_hi_int(h) : h_lo_int(h));
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 64) {
+    const int f = 2 * p0 + threadIdx.x;
+    if (f < F) {
+      const int p = f >> 1, b = f & 1;
+      const int cur = kf & 1;
+      const uint32_t act = s.act[cur * s.FP + p];
+      const uint32_t fail = s.fail[cur * s.FP + p];
+      const bool running = (act >> b) & 1u;
+      iters[f] = s.iters[f];
+      okf[f] = running ? (uint8_t)(((fail >> b) & 1u) ^ 1u) : (uint8_t)((s.ok[p] >> b) & 1u);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ float32
+
+struct F32S {
+  float* z;
+  float* acc;
+  uint4* st;
+  float* lm;
+  float* q0;
+  uint32_t* act;
+  uint32_t* fail;
+  int32_t* iters;
+  uint32_t* ok;
+  int FL;
+};
+
+F32S f32s_view(void* ws, const StreamLayout& L) {
+  char* b = static_cast<char*>(ws);
+  F32S s;
+  s.z = reinterpret_cast<float*>(b + L.z);
+  s.acc = reinterpret_cast<float*>(b + L.acc);
+  s.st = reinterpret_cast<uint4*>(b + L.st);
+  s.lm = reinterpret_cast<float*>(b + L.st);
+  s.q0 = reinterpret_cast<float*>(b + L.q0);
+  s.act = reinterpret_cast<uint32_t*>(b + L.act);
+  s.fail = reinterpret_cast<uint32_t*>(b + L.fail);
+  s.iters = reinterpret_cast<int32_t*>(b + L.iters);
+  s.ok = reinterpret_cast<uint32_t*>(b + L.ok);
+  s.FL = L.lanes;
+  return s;
+}
+
+__global__ void __launch_bounds__(256) f32s_init(const DevCode c, const float* __restrict__ llr, int32_t F,
+                                                 int32_t max_iter, F32S s) {
+  __shared__ float tile[32][65];  // [frame][variable]
+  const int n0 = blockIdx.x * 64, f0 = blockIdx.y * 32;
+  const int N = c.N;
+  for (int i = threadIdx.x; i < 32 * 64; i += blockDim.x) {
+    const int fl = i >> 6, nl = i & 63;
+    const int f = f0 + fl, n = n0 + nl;
+    tile[fl][nl] = (f < F && n < N) ? llr[(size_t)f * N + n] : 0.0f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+    const int nl = i >> 5, fl = i & 31;
+    const int n = n0 + nl;
+    if (n >= N) continue;
+    const size_t o = (size_t)n * s.FL + f0 + fl;
+    const float q = tile[fl][nl];
+    s.q0[o] = q;
+    s.z[o] = q;
+    s.acc[o] = q;
+  }
+  if (blockIdx.x == 0) {
+    for (int fl = threadIdx.x; fl < 32; fl += blockDim.x) {
+      const int f = f0 + fl;
+      s.act[s.FL + f] = f < F ? 1u : 0u;
+      s.act[f] = 0u;
+      s.fail[f] = 0u;
+      s.fail[s.FL + f] = 0u;
+      s.iters[f] = max_iter;
+      s.ok[f] = 0u;
+    }
+  }
+}
+
+template <int FORM, bool ES>
+__device__ __forceinline__ uint32_t f32s_check(const DevCode& c, const F32Rule& r, int m, int f, const F32S& s) {
+  const size_t FL = (size_t)s.FL;
+  const int e0 = __ldg(c.rp + m);
+  const int d = __ldg(c.rp + m + 1) - e0;
+  float A = 0.f, B = 0.f;
+  int I = 0;
+  uint32_t S = 0;
+  if constexpr (FORM == 1) {
+    const uint4 st = s.st[(size_t)m * FL + f];
+    A = __uint_as_float(st.x);
+    B = __uint_as_float(st.y);
+    I = (int)st.z;
+    S = st.w;
+  }
+  float mn1 = __int_as_float(0x7f800000), mn2 = __int_as_float(0x7f800000);
+  int idx = 0;
+  uint32_t neg = 0, par = 0;
+  for (int j = 0; j < d; ++j) {
+    const int n = __ldg(c.ci + e0 + j);
+    const float z = s.z[(size_t)n * FL + f];
+    float lold;
+    if constexpr (FORM == 1) {
+      const float mag = (j == I) ? B : A;
+      lold = ((S >> j) & 1u) ? -mag : mag;
+    } else {
+      lold = s.lm[(size_t)(e0 + j) * FL + f];
+    }
+    if (ES) par ^= (z <= 0.0f) ? 1u : 0u;
+    const float u = z - lold;
+    neg |= (u < 0.0f ? 1u : 0u) << j;
+    const float a = fabsf(u);
+    if (a < mn1) { mn2 = mn1; mn1 = a; idx = j; }
+    else if (a < mn2) { mn2 = a; }
+  }
+  const uint32_t dm = d >= 32 ? 0xffffffffu : ((1u << d) - 1u);
+  const uint32_t Sn = ((__popc(neg) & 1) ? ~neg : neg) & dm;
+  const float An = r.g(mn1), Bn = r.g(mn2);
+  for (int j = 0; j < d; ++j) {
+    const int n = __ldg(c.ci + e0 + j);
+    const float mag = (j == idx) ? Bn : An;
+    const float l = ((Sn >> j) & 1u) ? -mag : mag;
+    atomicAdd(s.acc + (size_t)n * FL + f, l);
+    if constexpr (FORM == 0) s.lm[(size_t)(e0 + j) * FL + f] = l;
+  }
+  if constexpr (FORM == 1)
+    s.st[(size_t)m * FL + f] = make_uint4(__float_as_uint(An), __float_as_uint(Bn), (uint32_t)idx, Sn);
+  return par;
+}
+
+template <int FORM, bool ES>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_rows(const DevCode c, const F32Rule r, F32S s, int k) {
+  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = s.FL / 32;
+  const int chunk = warp % n_chunks;
+  const int m0 = (warp / n_chunks) * kRowsPerWarp;
+  if (m0 >= c.M) return;
+  const int f = chunk * 32 + lane;
+  const int cur = k & 1;
+  if (__all_sync(0xffffffffu, s.act[cur * s.FL + f] == 0u)) return;
+  uint32_t fail = 0;
+  const int m1 = min(m0 + kRowsPerWarp, c.M);
+  for (int m = m0; m < m1; ++m) fail |= f32s_check<FORM, ES>(c, r, m, f, s);
+  if (ES && fail) atomicOr(s.fail + cur * s.FL + f, 1u);
+}
+
+template <bool ES>
+__global__ void __launch_bounds__(256) f32s_cols(const DevCode c, F32S s, int k) {
+  const int f = blockIdx.y * 32 + (threadIdx.x & 31);
+  const int cur = k & 1, nxt = cur ^ 1;
+  const uint32_t act = s.act[cur * s.FL + f];
+  const uint32_t stop = ES ? (act & (s.fail[cur * s.FL + f] ^ 1u)) : 0u;
+  const uint32_t cont = act & ~stop;
+  for (int n = blockIdx.x * 8 + (threadIdx.x >> 5); n < c.N; n += gridDim.x * 8) {
+    const size_t o = (size_t)n * s.FL + f;
+    if (cont) s.z[o] = s.acc[o];
+    s.acc[o] = s.q0[o];
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    s.act[nxt * s.FL + f] = cont;
+    s.fail[nxt * s.FL + f] = 0u;
+    if (ES && stop) {
+      s.iters[f] = k - 1;
+      s.ok[f] = 1u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_final_syndrome(const DevCode c, F32S s, int kf) {
+  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = s.FL / 32;
+  const int chunk = warp % n_chunks;
+  const int m0 = (warp / n_chunks) * kRowsPerWarp;
+  if (m0 >= c.M) return;
+  const int f = chunk * 32 + lane;
+  const int cur = kf & 1;
+  if (__all_sync(0xffffffffu, s.act[cur * s.FL + f] == 0u)) return;
+  uint32_t fail = 0;
+  const int m1 = min(m0 + kRowsPerWarp, c.M);
+  for (int m = m0; m < m1; ++m) {
+    uint32_t y = 0;
+    for (int e = __ldg(c.rp + m); e < __ldg(c.rp + m + 1); ++e)
+      y ^= (s.z[(size_t)__ldg(c.ci + e) * s.FL + f] <= 0.0f) ? 1u : 0u;
+    fail |= y;
+  }
+  if (fail) atomicOr(s.fail + cur * s.FL + f, 1u);
+}
+
+__global__ void __launch_bounds__(256) f32s_output(const DevCode c, F32S s, int kf, int32_t F, uint8_t* bits,
+                                                   int32_t* iters, uint8_t* okf, float* zout) {
+  __shared__ float tile[64][33];  // [variable][frame]
+  const int n0 = blockIdx.x * 64, f0 = blockIdx.y * 32;
+  const int N = c.N, N8 = (N + 7) >> 3;
+  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+    const int nl = i >> 5, fl = i & 31;
+    const int n = n0 + nl;
+    tile[nl][fl] = n < N ? s.z[(size_t)n * s.FL + f0 + fl] : 0.0f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * 8; i += blockDim.x) {
+    const int fl = i >> 3, bl = i & 7;
+    const int f = f0 + fl, b = (n0 >> 3) + bl;
+    if (f >= F || b >= N8) continue;
+    uint32_t byte = 0;
+    for (int t = 0; t < 8; ++t) {
+      const int nl = bl * 8 + t;
+      if (n0 + nl < N) byte |= (tile[nl][fl] <= 0.0f ? 1u : 0u) << t;
+    }
+    bits[(size_t)f * N8 + b] = (uint8_t)byte;
+  }
+  if (zout != nullptr) {
+    for (int i = threadIdx.x; i < 32 * 64; i += blockDim.x) {
+      const int fl = i >> 6, nl = i & 63;
+      const int f = f0 + fl, n = n0 + nl;
+      if (f < F && n < N) zout[(size_t)f * N + n] = tile[nl][fl];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    const int f = f0 + threadIdx.x;
+    if (f < F) {
+      const int cur = kf & 1;
+      const bool running = s.act[cur * s.FL + f] != 0u;
+      iters[f] = s.iters[f];
+      okf[f] = running ? (uint8_t)(s.fail[cur * s.FL + f] ^ 1u) : (uint8_t)s.ok[f];
+    }
+  }
+}
+
+int rows_grid(int M, int lanes) {
+  const int64_t warps = (int64_t)((M + kRowsPerWarp - 1) / kRowsPerWarp) * (lanes / 32);
+  return (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+}
+
+template <int FORM, bool ES>
+cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H2S s, int sm_count, int32_t F,
+                    int32_t max_iter, cudaStream_t st) {
+  const int rgrid = rows_grid(c.M, L.lanes);
+  const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
+                   L.lanes / 32);
+  (void)F;
+  for (int k = 1; k <= max_iter; ++k) {
+    h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+    h2s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k);
+  }
+  return cudaGetLastError();
+}
+
+template <int FORM, bool ES>
+cudaError_t f32s_run(const DevCode& c, const F32Rule& r, const StreamLayout& L, F32S s, int sm_count,
+                     int32_t max_iter, cudaStream_t st) {
+  const int rgrid = rows_grid(c.M, L.lanes);
+  const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
+                   L.lanes / 32);
+  for (int k = 1; k <= max_iter; ++k) {
+    f32s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+    f32s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t stream_int8_decode(const DevCode& c, const IntRule& r, int form, const StreamLayout& L, void* ws,
+                               int sm_count, const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop,
+                               uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
+  H2S s = h2s_view(ws, L);
+  const dim3 tgrid((c.N + 63) / 64, L.lanes / 32);
+  // L^(0) = 0: Section V state all zero, per-edge bytes L + 128 = 0x80
+  cudaError_t e0 = cudaMemsetAsync(static_cast<char*>(ws) + L.st, form == 1 ? 0 : 0x80, L.q0 - L.st, st);
+  if (e0 != cudaSuccess) return e0;
+  h2s_init<<<tgrid, 256, 0, st>>>(c, llr, F, max_iter, s);
+  cudaError_t e;
+  const bool es = early_stop != 0;
+  if (form == 1) e = es ? h2s_run<1, true>(c, r, L, s, sm_count, F, max_iter, st)
+                        : h2s_run<1, false>(c, r, L, s, sm_count, F, max_iter, st);
+  else e = es ? h2s_run<0, true>(c, r, L, s, sm_count, F, max_iter, st)
+              : h2s_run<0, false>(c, r, L, s, sm_count, F, max_iter, st);
+  if (e != cudaSuccess) return e;
+  const int kf = max_iter + 1;
+  h2s_final_syndrome<<<rows_grid(c.M, L.lanes), kWarpsPerBlock * 32, 0, st>>>(c, s, kf);
+  h2s_output<<<tgrid, 256, 0, st>>>(c, s, kf, F, bits, iters, ok, zout);
+  return cudaGetLastError();
+}
+
+cudaError_t stream_f32_decode(const DevCode& c, const F32Rule& r, int form, const StreamLayout& L, void* ws,
+                              int sm_count, const float* llr, int32_t F, int32_t max_iter, int32_t early_stop,
+                              uint8_t* bits, int32_t* iters, uint8_t* ok, float* zout, cudaStream_t st) {
+  F32S s = f32s_view(ws, L);
+  const dim3 tgrid((c.N + 63) / 64, L.lanes / 32);
+  cudaError_t e0 = cudaMemsetAsync(static_cast<char*>(ws) + L.st, 0, L.q0 - L.st, st);  // L^(0) = 0
+  if (e0 != cudaSuccess) return e0;
+  f32s_init<<<tgrid, 256, 0, st>>>(c, llr, F, max_iter, s);
+  cudaError_t e;
+  const bool es = early_stop != 0;
+  if (form == 1) e = es ? f32s_run<1, true>(c, r, L, s, sm_count, max_iter, st)
+                        : f32s_run<1, false>(c, r, L, s, sm_count, max_iter, st);
+  else e = es ? f32s_run<0, true>(c, r, L, s, sm_count, max_iter, st)
+              : f32s_run<0, false>(c, r, L, s, sm_count, max_iter, st);
+  if (e != cudaSuccess) return e;
+  const int kf = max_iter + 1;
+  f32s_final_syndrome<<<rows_grid(c.M, L.lanes), kWarpsPerBlock * 32, 0, st>>>(c, s, kf);
+  f32s_output<<<tgrid, 256, 0, st>>>(c, s, kf, F, bits, iters, ok, zout);
+  return cudaGetLastError();
+}
+
+}  // namespace ldpc

@@ -27,8 +27,9 @@ LDPC_RULE_PLAIN, LDPC_RULE_OFFSET, LDPC_RULE_NORMALIZED = 0, 1, 2
 DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_F32}
 FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
 RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED}
-LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF = 0, 1, 2
-KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF}
+LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM = 0, 1, 2, 3
+KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF,
+           "stream": LDPC_KERNEL_STREAM}
 
 # Every symbol include/ldpc_gb300.h declares.
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",

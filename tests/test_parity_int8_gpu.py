@@ -142,13 +142,13 @@ def test_forced_kernel_rejects_ineligible_code(L):
     assert e.value.status == L.LDPC_ERR_UNSUPPORTED
 
 
-def test_unsupported_code_reports_cleanly(L):
-    """A code whose frame state exceeds one SM is reported, not run."""
+def test_frame_resident_kernels_reject_large_code(L):
+    """A code whose frame state exceeds one SM cannot be forced onto an on-chip kernel."""
     w = I.make_workload("irr_n64800", n_frames=1, with_llr=False)
     h = L.Code.from_inputs(w.code)
     import torch
     q = torch.zeros((2, w.code.n_vars), dtype=torch.int8, device="cuda")
-    try:
-        L.decode(h, q, L.make_params(**w.params))
-    except L.LdpcError as e:
-        assert e.status == L.LDPC_ERR_UNSUPPORTED
+    for kern in ("onchip_half", "onchip_int"):
+        with pytest.raises(L.LdpcError) as e:
+            L.decode(h, q, L.make_params(kernel=kern, **w.params))
+        assert e.value.status == L.LDPC_ERR_UNSUPPORTED

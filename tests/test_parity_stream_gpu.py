@@ -1,0 +1,164 @@
+"""GPU vs oracle parity of the device-memory (streaming) decoders: the int8 path
+(bit-exact, packed binary16 lanes) and the float32 path (within tolerance of the
+FP64 oracle; float atomics make the summation order vary)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_cs_0609090_gb300 import inputs as I
+from gpu_helpers import FORMS_INT, assert_int_parity, gpu_decode, oracle_int
+
+pytestmark = pytest.mark.gpu
+
+# |Z_gpu - Z_fp64| <= RTOL * max(1, |Z_fp64|) for the float32 normalized path:
+# lambda < 1 scales every rounding error down at each check.  Offset messages are
+# 1-Lipschitz in their inputs without that contraction, so float32 rounding grows
+# along the iterations; their bound is RTOL_OFFSET (measured <= 1.2e-4 after 30).
+RTOL = 1e-5
+RTOL_OFFSET = 5e-4
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_cs_0609090_gb300 import ldpc
+    return ldpc
+
+
+def _int(L, code, q0, form, p, kernel="stream"):
+    h = L.Code.from_inputs(code)
+    g = gpu_decode(h, code.n_vars, q0, L.make_params(form=form, kernel=kernel, **p))
+    assert_int_parity(g, oracle_int(code, q0, form, p))
+    return g
+
+
+@pytest.mark.parametrize("form", FORMS_INT)
+@pytest.mark.parametrize("early_stop", [1, 0])
+def test_int8_stream_small_codes(L, form, early_stop):
+    w = I.make_workload("reg36_n1008", n_frames=301, ebn0_db=1.8)
+    _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop))
+    w = I.make_workload("qc_n7493", n_frames=67, ebn0_db=2.0)
+    _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop))
+
+
+@pytest.mark.parametrize("form", FORMS_INT)
+def test_int8_stream_edge_cases(L, form):
+    w = I.make_workload("reg36_n1008", n_frames=65, ebn0_db=1.0)
+    for F in (1, 2, 33, 65):
+        _int(L, w.code, w.q0[:F], form, w.params)
+    _int(L, w.code, w.q0[:5], form, dict(w.params, max_iter=0))
+    g = _int(L, w.code, I.noiseless(w.codewords, 31), form, w.params)
+    assert np.all(g["iters"] == 0)
+
+
+@pytest.mark.parametrize("form", FORMS_INT)
+@pytest.mark.parametrize("early_stop", [1, 0])
+def test_int8_irregular_64800(L, form, early_stop):
+    """The N=64800 code does not fit one SM: the library picks the streaming kernel."""
+    w = I.make_workload("irr_n64800", n_frames=6, frame_seed=3)
+    p = dict(w.params, early_stop=early_stop)
+    _int(L, w.code, w.q0, form, p, kernel="auto")
+    if early_stop:
+        q = I.noiseless(w.codewords[:2], 127)
+        g = _int(L, w.code, q, form, p, kernel="auto")
+        assert np.all(g["iters"] == 0)
+
+
+def _f32(L, code, llr, form, rule, lam=0.75, offset=0.0, max_iter=50, early_stop=0, kernel="stream"):
+    import torch
+    h = L.Code.from_inputs(code)
+    params = L.make_params(dtype="f32", form=form, rule=rule, norm_f32=lam, offset_f32=offset,
+                           max_iter=max_iter, early_stop=early_stop, kernel=kernel)
+    t = torch.from_numpy(np.ascontiguousarray(llr, dtype=np.float32)).cuda()
+    bits, iters, ok, z = L.decode(h, t, params, want_llr=True)
+    torch.cuda.synchronize()
+    g = dict(bits=L.unpack_bits(bits.cpu().numpy(), code.n_vars), iters=iters.cpu().numpy(),
+             ok=ok.cpu().numpy(), z=z.cpu().numpy())
+    o = oracle.decode_f64(code, llr.astype(np.float32).astype(np.float64), form=form, rule=rule, lam=lam,
+                          offset=offset, max_iter=max_iter, early_stop=early_stop, want_margin=True)
+    return g, o
+
+
+def test_f32_hamming_golden(L):
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hamming74_min_sum.json")))
+    code = I.from_rows(7, gold["code"]["rows"])
+    q = np.array([gold["q0"]] * 3, dtype=np.float64)
+    for form in FORMS_INT:
+        g, _ = _f32(L, code, q, form, "normalized", max_iter=1)
+        assert g["z"][0].tolist() == gold["normalized_float_0p75"]["Z1"]
+        g, _ = _f32(L, code, q, form, "plain", max_iter=2)
+        assert g["z"][0].tolist() == gold["plain"]["Z2"]
+
+
+@pytest.mark.parametrize("form", FORMS_INT)
+def test_f32_irregular_64800_normalized(L, form):
+    w = I.make_workload("irr_n64800", n_frames=5, frame_seed=7)
+    g, o = _f32(L, w.code, w.llr, form, "normalized", max_iter=50, kernel="auto")
+    err = np.abs(g["z"] - o.z) / np.maximum(1.0, np.abs(o.z))
+    assert err.max() <= RTOL, f"max relative error {err.max():.3g}"
+    assert np.array_equal(g["iters"], o.iters)
+    nz = np.abs(o.z) > 1e-3
+    assert np.array_equal(g["bits"][nz], o.bits[nz])
+
+
+# Frames whose FP64 posteriors come within this distance of the decision rule
+# (min over iterations of |Z_n|) may legitimately stop at another iteration or
+# decide a bit differently under float32 rounding.
+MARGIN = 1e-4
+
+
+@pytest.mark.parametrize("form", FORMS_INT)
+@pytest.mark.parametrize("rule,offset", [("offset", 0.5), ("normalized", 0.0)])
+def test_f32_early_stop_regular(L, form, rule, offset):
+    """Frames away from the decision boundary: iteration counts, flags and
+    decisions equal the FP64 oracle's.  Frames the oracle decodes to a codeword
+    (a contractive trajectory) also have posteriors within RTOL; frames that run
+    to the cap without one are excluded from that check (rounding can grow along
+    their oscillating trajectory)."""
+    w = I.make_workload("reg36_n1008", n_frames=400, ebn0_db=2.0)
+    g, o = _f32(L, w.code, w.llr, form, rule, offset=offset, max_iter=30, early_stop=1)
+    clean = o.margin >= MARGIN
+    assert clean.sum() >= 0.9 * clean.size, f"{(~clean).sum()} near-tie frames"
+    assert np.array_equal(g["iters"][clean], o.iters[clean])
+    assert np.array_equal(g["ok"][clean], o.ok[clean])
+    assert np.array_equal(g["bits"][clean], o.bits[clean])
+    conv = clean & (o.ok == 1)
+    assert conv.sum() >= 0.8 * clean.size
+    err = np.abs(g["z"][conv] - o.z[conv]) / np.maximum(1.0, np.abs(o.z[conv]))
+    tol = RTOL_OFFSET if rule == "offset" else RTOL
+    assert err.max() <= tol, f"max relative error {err.max():.3g}"
+
+
+def test_stream_workspace_contract(L):
+    import torch
+    w = I.make_workload("irr_n64800", n_frames=2)
+    h = L.Code.from_inputs(w.code)
+    params = L.make_params(**w.params)
+    need = L.ldpc_workspace_size(h.handle, params, 2)
+    assert need > 0
+    q = torch.from_numpy(w.q0).cuda()
+    bits = torch.empty((2, (w.code.n_vars + 7) // 8), dtype=torch.uint8, device="cuda")
+    it = torch.empty(2, dtype=torch.int32, device="cuda")
+    ok = torch.empty(2, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) & ~255
+
+    class P:
+        def __init__(self, v):
+            self.v = v
+
+        def data_ptr(self):
+            return self.v
+    with pytest.raises(L.LdpcError) as e:        # too small
+        L.ldpc_decode_batch(h.handle, params, q, 2, bits, it, ok, None, P(base), need - 1)
+    assert e.value.status == L.LDPC_ERR_INVALID_ARG
+    with pytest.raises(L.LdpcError) as e:        # misaligned
+        L.ldpc_decode_batch(h.handle, params, q, 2, bits, it, ok, None, P(base + 16), need)
+    assert e.value.status == L.LDPC_ERR_INVALID_ARG
+    L.ldpc_decode_batch(h.handle, params, q, 2, bits, it, ok, None, P(base), need)
+    torch.cuda.synchronize()
