@@ -151,6 +151,43 @@ LDPC_API ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_
                               int32_t *iters_used, uint8_t *syndrome_ok, void *llr_out,
                               void *workspace, size_t ws_bytes, void *stream);
 
+/* Size of the device scratch array built into the library for
+ * ldpc_decode_batch_noalloc (held on every GPU that loads the library). */
+#define LDPC_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+
+/* ldpc_decode_batch for callers that cannot allocate device memory.  (An
+ * interface of this library; the paper has no counterpart.)
+ *
+ * Who needs it: decode paths that must not call cudaMalloc -- a receiver with a
+ * bounded per-block latency (cudaMalloc synchronises the device and can take
+ * arbitrarily long), or a component that only gets buffers from a pool it does
+ * not own -- and so cannot provide ldpc_decode_batch's workspace.  This entry
+ * point allocates nothing: it runs the int8 single-scan streaming decoder
+ * (LDPC_KERNEL_STREAM) on LDPC_NOALLOC_SCRATCH_BYTES of scratch compiled into
+ * the library as a device array.  The caller still passes the inputs and
+ * outputs, with the meanings of ldpc_decode_batch; results are identical to
+ * ldpc_decode_batch with kernel = LDPC_KERNEL_STREAM.
+ *
+ * Limits and behaviour:
+ *  - params->dtype must be LDPC_DTYPE_INT8, form SS_FIXED or SS_1BIT, kernel AUTO
+ *    or STREAM; otherwise LDPC_ERR_UNSUPPORTED.
+ *  - A request whose scratch exceeds LDPC_NOALLOC_SCRATCH_BYTES is rejected with
+ *    LDPC_ERR_UNSUPPORTED and a message giving both sizes; decode fewer frames
+ *    per call.  (48 MiB holds 64 frames of an N = 64800, rate-1/2 code, or about
+ *    780 frames of the N = 7493 code.)
+ *  - The first call on a device looks up the array's device address (a CUDA
+ *    runtime query, no allocation); make that first call before any stream
+ *    capture on the device.
+ *  - Every call on a device uses the same array and leaves its contents behind;
+ *    the decoder initialises everything it reads.  Calls whose executions
+ *    overlap on the GPU (different streams, or different host threads) race on
+ *    the array and corrupt each other: serialise them.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called. */
+LDPC_API ldpc_status ldpc_decode_batch_noalloc(const ldpc_code *code, const ldpc_decode_params *params,
+                                               const void *llr, int32_t n_frames, uint8_t *hard_bits,
+                                               int32_t *iters_used, uint8_t *syndrome_ok, void *llr_out,
+                                               void *stream);
+
 /* Message describing the last failed call on this thread ("" if none). */
 LDPC_API const char *ldpc_last_error(void);
 

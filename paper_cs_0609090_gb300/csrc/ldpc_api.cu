@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -357,6 +358,90 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
                                      static_cast<int16_t*>(llr_out), st);
   }
   if (err != cudaSuccess) return cuda_fail(err, "ldpc_decode_batch launch");
+  return LDPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Decoding without any device allocation by the caller or the library.
+//
+// Some callers cannot allocate device memory on their decode path: a receiver
+// that must keep a bounded per-block latency cannot afford cudaMalloc (it
+// synchronises the device and its latency is unbounded), and a host component
+// that only receives buffers from a memory pool it does not own has no
+// allocator to call.  For them ldpc_decode_batch_noalloc runs the streaming int8
+// decoder on a scratch area that is part of the library image itself: a
+// file-scope device array, created once on every GPU that loads the library and
+// kept until the process exits.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[LDPC_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).  In
+// host code the array's name is only a host-side stand-in, so its device
+// address is looked up once per device and cached.
+ldpc_status noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kNoallocMaxDevices)
+    return fail(LDPC_ERR_UNSUPPORTED, "device %d is beyond the %d devices the static scratch supports", device,
+                kNoallocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[device] == nullptr) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = g_noalloc_ptr[device];
+  return LDPC_OK;
+}
+
+}  // namespace
+
+ldpc_status ldpc_decode_batch_noalloc(const ldpc_code* code, const ldpc_decode_params* params, const void* llr,
+                                      int32_t n_frames, uint8_t* hard_bits, int32_t* iters_used,
+                                      uint8_t* syndrome_ok, void* llr_out, void* stream) {
+  g_last_error.clear();
+  if (code == nullptr || params == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code and params must be non-NULL");
+  if (n_frames < 0) return fail(LDPC_ERR_INVALID_ARG, "n_frames %d < 0", n_frames);
+  ldpc_status s = check_params(code, params);
+  if (s != LDPC_OK) return s;
+  if (params->dtype != LDPC_DTYPE_INT8 || params->form == LDPC_FORM_TWO_SCAN ||
+      (params->kernel != LDPC_KERNEL_AUTO && params->kernel != LDPC_KERNEL_STREAM))
+    return fail(LDPC_ERR_UNSUPPORTED, "the no-allocation entry point runs the int8 single-scan streaming decoder only");
+  if (!ldpc::stream_int8_eligible(code->max_row_deg, code->max_col_deg, params->msg_sat))
+    return fail(LDPC_ERR_UNSUPPORTED, "code degrees / msg_sat are outside the streaming int8 decoder's range");
+  if (n_frames == 0) return LDPC_OK;
+  if (llr == nullptr || hard_bits == nullptr || iters_used == nullptr || syndrome_ok == nullptr)
+    return fail(LDPC_ERR_INVALID_ARG, "llr, hard_bits, iters_used and syndrome_ok must be non-NULL");
+  const int form = params->form == LDPC_FORM_SS_1BIT ? 1 : 0;
+  const ldpc::StreamLayout L = ldpc::stream_layout(0, form, code->N, code->M, code->E, n_frames);
+  if (L.total > (size_t)LDPC_NOALLOC_SCRATCH_BYTES)
+    return fail(LDPC_ERR_UNSUPPORTED,
+                "%d frames of this code need %zu bytes of scratch; the static scratch holds %zu "
+                "(decode fewer frames per call)",
+                n_frames, L.total, (size_t)LDPC_NOALLOC_SCRATCH_BYTES);
+  DeviceGuard guard(code->device);
+  if (!guard.ok) return fail(LDPC_ERR_CUDA, "cudaSetDevice(%d) failed", code->device);
+  void* scratch = nullptr;
+  s = noalloc_scratch(code->device, &scratch);
+  if (s != LDPC_OK) return s;
+  ldpc::IntRule r;
+  r.rule = params->rule;
+  r.beta = params->offset;
+  r.num = params->norm_num;
+  r.shift = params->norm_shift;
+  r.qm = params->msg_sat;
+  // every buffer the decoder reads before writing is initialised by the decoder
+  // itself (state memset, init kernel), so contents left by a previous call do not matter
+  const cudaError_t err = ldpc::stream_int8_decode(view(code), r, form, L, scratch, code->sm_count,
+                                                   static_cast<const int8_t*>(llr), n_frames, params->max_iter,
+                                                   params->early_stop, hard_bits, iters_used, syndrome_ok,
+                                                   static_cast<int16_t*>(llr_out), (cudaStream_t)stream);
+  if (err != cudaSuccess) return cuda_fail(err, "ldpc_decode_batch_noalloc launch");
   return LDPC_OK;
 }
 

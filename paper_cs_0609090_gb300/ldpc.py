@@ -33,7 +33,8 @@ KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onch
 
 # Every symbol include/ldpc_gb300.h declares.
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",
-           "ldpc_decode_batch", "ldpc_last_error")
+           "ldpc_decode_batch", "ldpc_decode_batch_noalloc", "ldpc_last_error")
+NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
 class LdpcError(RuntimeError):
@@ -58,6 +59,8 @@ _lib.ldpc_workspace_size.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), cty
                                      ctypes.POINTER(ctypes.c_size_t)]
 _lib.ldpc_decode_batch.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), _P, ctypes.c_int32, _P, _P, _P,
                                    _P, _P, ctypes.c_size_t, _P]
+_lib.ldpc_decode_batch_noalloc.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), _P, ctypes.c_int32, _P, _P,
+                                           _P, _P, _P]
 _lib.ldpc_last_error.restype = ctypes.c_char_p
 for _f in EXPORTS[:-1]:
     getattr(_lib, _f).restype = ctypes.c_int32
@@ -138,6 +141,17 @@ def ldpc_decode_batch(code: int, params: ldpc_decode_params, llr, n_frames: int,
     _check(_lib.ldpc_decode_batch(_P(code), ctypes.byref(params), _ptr(llr), int(n_frames), _ptr(hard_bits),
                                   _ptr(iters_used), _ptr(syndrome_ok), _ptr(llr_out), _ptr(workspace),
                                   int(ws_bytes), _stream_handle(stream)), "ldpc_decode_batch")
+
+
+def ldpc_decode_batch_noalloc(code: int, params: ldpc_decode_params, llr, n_frames: int, hard_bits, iters_used,
+                              syndrome_ok, llr_out=None, stream=None) -> None:
+    """ldpc_decode_batch for callers that cannot allocate device memory: the
+    library's built-in device scratch replaces the workspace (int8 streaming
+    decoder; see include/ldpc_gb300.h for the size limit and the rule that calls
+    overlapping on the GPU race)."""
+    _check(_lib.ldpc_decode_batch_noalloc(_P(code), ctypes.byref(params), _ptr(llr), int(n_frames), _ptr(hard_bits),
+                                          _ptr(iters_used), _ptr(syndrome_ok), _ptr(llr_out),
+                                          _stream_handle(stream)), "ldpc_decode_batch_noalloc")
 
 
 class Code:
