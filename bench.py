@@ -233,6 +233,8 @@ def main():
     kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel"}.get(args.kernel)
     if ws_bytes > 0:
         kname = "f32s_rows" if args.dtype == "f32" else "h2s_rows"
+    elif args.form == "two_scan":
+        kname = "onchip_twoscan_kernel"
     elif kname is None:
         info = ldpc.ldpc_code_info(code.handle)
         half_ok = info["max_row_degree"] <= 16 and \

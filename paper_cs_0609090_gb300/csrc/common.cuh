@@ -18,6 +18,10 @@ struct DevCode {
   const int32_t* __restrict__ ell32;
   const uint8_t* __restrict__ rdeg;  // [M] check degrees |N(m)|
   int32_t ell_w;
+  // Variable->check adjacency M(n) for the two-scan comparator only: the edge
+  // slots (j * M + m) of variable n are cslot[cptr[n] .. cptr[n+1]-1].
+  const int32_t* __restrict__ cptr;   // [N+1]
+  const int32_t* __restrict__ cslot;  // [E]
   __device__ __forceinline__ int col(int j, int m) const {
     return ell16 != nullptr ? (int)__ldg(ell16 + (size_t)j * M + m) : __ldg(ell32 + (size_t)j * M + m);
   }

@@ -43,6 +43,13 @@ cudaError_t onchip_h2_launch(const DevCode& c, const IntRule& r, int form, Onchi
                              const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
                              int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t stream, bool occupancy_only);
 
+// Two-scan comparator (Section III), frame-resident, exact binary16 pairs.
+bool onchip_twoscan_plan(const DevCode& c, int32_t n_frames, int sm_count, size_t smem_optin, int max_row_deg,
+                         OnchipPlan* plan);
+cudaError_t onchip_twoscan_launch(const DevCode& c, const IntRule& r, OnchipPlan& plan, int sm_count,
+                                  const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
+                                  int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t stream);
+
 // Device-memory (streaming) decoders for codes whose frame state does not fit
 // one SM.  All state lives in the caller's workspace (layout below).
 struct StreamLayout {

@@ -20,6 +20,8 @@ struct ldpc_code {
   uint16_t* d_ell16 = nullptr;
   int32_t* d_ell32 = nullptr;
   uint8_t* d_rdeg = nullptr;
+  int32_t* d_cptr = nullptr;
+  int32_t* d_cslot = nullptr;
   int32_t ell_w = 0;
   int sm_count = 0;
   size_t smem_optin = 0;
@@ -72,6 +74,8 @@ ldpc::DevCode view(const ldpc_code* c) {
   v.ell32 = c->d_ell32;
   v.rdeg = c->d_rdeg;
   v.ell_w = c->ell_w;
+  v.cptr = c->d_cptr;
+  v.cslot = c->d_cslot;
   return v;
 }
 
@@ -112,7 +116,7 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
 
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
-  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, STREAM_INT8, STREAM_F32 } kind = NONE;
+  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, STREAM_INT8, STREAM_F32, ONCHIP_TWOSCAN } kind = NONE;
   ldpc::OnchipPlan onchip;
   ldpc::StreamLayout stream;
   size_t ws = 0;
@@ -145,6 +149,18 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     return fail(LDPC_ERR_UNSUPPORTED, "code (N=%d, M=%d, E=%d, row degree <= %d, column degree <= %d) "
                 "cannot run on the requested frame-resident kernel (%d)",
                 c->N, c->M, c->E, c->max_row_deg, c->max_col_deg, p->kernel);
+  }
+  if (p->dtype == LDPC_DTYPE_INT8 && p->form == LDPC_FORM_TWO_SCAN) {
+    if ((p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF) &&
+        ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat) &&
+        ldpc::onchip_twoscan_plan(v, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
+      ch->kind = Choice::ONCHIP_TWOSCAN;
+      ch->ws = 0;
+      return LDPC_OK;
+    }
+    return fail(LDPC_ERR_UNSUPPORTED, "the two-scan comparator needs a code whose edge cells fit one SM "
+                "(N=%d, E=%d) with row degree <= 16 and 128 + (max_col_degree + 1) * msg_sat <= 2048",
+                c->N, c->E);
   }
   if (p->dtype == LDPC_DTYPE_F32 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED) &&
       (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM)) {
@@ -200,6 +216,15 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   std::vector<uint16_t> ell16(narrow ? (size_t)max_row * n_checks : 0);
   std::vector<int32_t> ell32(narrow ? 0 : (size_t)max_row * n_checks);
   std::vector<uint8_t> rdeg((size_t)n_checks);
+  // variable -> edge slots (j * M + m), in increasing m, for the two-scan comparator
+  std::vector<int32_t> cptr((size_t)n_vars + 1, 0), cslot((size_t)E), cfill((size_t)n_vars, 0);
+  for (int32_t e = 0; e < E; ++e) cptr[(size_t)col_idx[e] + 1]++;
+  for (int32_t n = 0; n < n_vars; ++n) cptr[(size_t)n + 1] += cptr[(size_t)n];
+  for (int32_t m = 0; m < n_checks; ++m)
+    for (int32_t j = 0; j < row_ptr[m + 1] - row_ptr[m]; ++j) {
+      const int32_t n = col_idx[row_ptr[m] + j];
+      cslot[(size_t)(cptr[(size_t)n] + cfill[(size_t)n]++)] = j * n_checks + m;
+    }
   for (int32_t m = 0; m < n_checks; ++m) {
     const int32_t d = row_ptr[m + 1] - row_ptr[m];
     rdeg[(size_t)m] = (uint8_t)d;
@@ -235,6 +260,12 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
       (err = cudaMalloc(&c->d_cdeg, sizeof(int32_t) * (size_t)n_vars)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_cdeg, col_deg.data(), sizeof(int32_t) * (size_t)n_vars, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
+      (err = cudaMalloc(&c->d_cptr, sizeof(int32_t) * ((size_t)n_vars + 1))) != cudaSuccess ||
+      (err = cudaMemcpy(c->d_cptr, cptr.data(), sizeof(int32_t) * ((size_t)n_vars + 1), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (err = cudaMalloc(&c->d_cslot, sizeof(int32_t) * (size_t)E)) != cudaSuccess ||
+      (err = cudaMemcpy(c->d_cslot, cslot.data(), sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
       (err = cudaMalloc(&c->d_rdeg, (size_t)n_checks)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_rdeg, rdeg.data(), (size_t)n_checks, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (narrow && (err = cudaMalloc(&c->d_ell16, sizeof(uint16_t) * ell16.size())) != cudaSuccess) ||
@@ -252,6 +283,8 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
     cudaFree(c->d_rdeg);
     cudaFree(c->d_ell16);
     cudaFree(c->d_ell32);
+    cudaFree(c->d_cptr);
+    cudaFree(c->d_cslot);
     delete c;
     return cuda_fail(err, "ldpc_code_create device copy");
   }
@@ -270,6 +303,8 @@ ldpc_status ldpc_code_destroy(ldpc_code* code) {
   cudaFree(code->d_rdeg);
   cudaFree(code->d_ell16);
   cudaFree(code->d_ell32);
+  cudaFree(code->d_cptr);
+  cudaFree(code->d_cslot);
   delete code;
   return LDPC_OK;
 }
@@ -334,7 +369,11 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
   r.shift = params->norm_shift;
   r.qm = params->msg_sat;
   const int form = params->form == LDPC_FORM_SS_1BIT ? 1 : 0;
-  if (ch.kind == Choice::ONCHIP_H2) {
+  if (ch.kind == Choice::ONCHIP_TWOSCAN) {
+    err = ldpc::onchip_twoscan_launch(v, r, ch.onchip, code->sm_count, static_cast<const int8_t*>(llr), n_frames,
+                                      params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
+                                      static_cast<int16_t*>(llr_out), st);
+  } else if (ch.kind == Choice::ONCHIP_H2) {
     err = ldpc::onchip_h2_launch(v, r, form, ch.onchip, code->sm_count, static_cast<const int8_t*>(llr), n_frames,
                                  params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
                                  static_cast<int16_t*>(llr_out), st, false);

@@ -152,3 +152,29 @@ def test_frame_resident_kernels_reject_large_code(L):
         with pytest.raises(L.LdpcError) as e:
             L.decode(h, q, L.make_params(kernel=kern, **w.params))
         assert e.value.status == L.LDPC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("early_stop", [1, 0])
+def test_two_scan_comparator(L, early_stop):
+    """The GPU two-scan comparator (Eqs. (1)-(2)) against the oracle's literal two-scan."""
+    for wl, F, eb in (("reg36_n1008", 300, 1.8), ("qc_n7493", 45, 2.0)):
+        w = I.make_workload(wl, n_frames=F, ebn0_db=eb)
+        _run(L, w.code, w.q0, "two_scan", dict(w.params, early_stop=early_stop))
+    w = I.make_workload("reg36_n1008", n_frames=5, ebn0_db=1.0)
+    _run(L, w.code, w.q0[:1], "two_scan", dict(w.params, early_stop=early_stop))
+    _run(L, w.code, w.q0, "two_scan", dict(w.params, max_iter=0, early_stop=early_stop))
+
+
+def test_two_scan_hamming_and_tree(L):
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hamming74_min_sum.json")))
+    code = I.from_rows(7, gold["code"]["rows"])
+    h = L.Code.from_inputs(code)
+    q0 = np.array([gold["q0"]] * 3, dtype=np.int8)
+    g = gpu_decode(h, 7, q0, L.make_params(form="two_scan", rule="plain", max_iter=2, early_stop=0))
+    assert g["z"][0].tolist() == gold["plain"]["Z2"]
+    tc = I.tree_code(16, 4)
+    rng = np.random.default_rng(4)
+    q = rng.integers(-20, 21, size=(17, 16)).astype(np.int8)
+    _run(L, tc, q, "two_scan", dict(rule="plain", msg_sat=127, max_iter=32, early_stop=0))
+    _run(L, tc, q, "two_scan", dict(rule="normalized", norm_num=3, norm_shift=2, msg_sat=100, max_iter=9))
