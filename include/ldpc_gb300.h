@@ -151,6 +151,80 @@ LDPC_API ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_
                               int32_t *iters_used, uint8_t *syndrome_ok, void *llr_out,
                               void *workspace, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned offset min-sum (an extension of Section III's offset rule: beta_k
+ * becomes a trainable table beta[k][c], c = degree class of the check), the
+ * hand-written adjoint through the unrolled iterations, and the pieces of a
+ * training step.  The decoder is the Section V single scan in float32.
+ * ------------------------------------------------------------------------ */
+
+/* Degree classes of a code: the distinct check degrees in ascending order.
+ * degrees (host, nullable) receives n_classes entries (at most 31). */
+LDPC_API ldpc_status ldpc_code_degree_classes(const ldpc_code *code, int32_t *n_classes, int32_t *degrees);
+
+/* Bytes of device workspace that ldpc_learned_forward / _loss / _backward share
+ * for n_iters iterations and n_frames frames: per-iteration checkpoints of the
+ * posteriors Z^(k) and the Section V state, plus gradient buffers. */
+LDPC_API ldpc_status ldpc_learned_workspace_size(const ldpc_code *code, int32_t n_iters, int32_t n_frames,
+                                                 size_t *bytes);
+
+/* Forward: n_iters (1..64) iterations of the Section V single scan with the
+ * offset |L| <- max(|L| - beta[k][c], 0), no early stop.
+ *   beta      device, [n_iters][n_classes] float32, iteration-major.
+ *   llr       device, [n_frames][n_vars] float32 channel values Z0.
+ *   z_out     device or NULL, [n_frames][n_vars] final posterior Z^(n_iters).
+ *   workspace device, >= ldpc_learned_workspace_size bytes, 256-byte aligned;
+ *             it keeps the checkpoints that _loss and _backward read, so those
+ *             calls must use the same workspace, n_iters and n_frames.
+ * Codes with more than 4 degree classes: LDPC_ERR_UNSUPPORTED. */
+LDPC_API ldpc_status ldpc_learned_forward(const ldpc_code *code, int32_t n_iters, const float *beta,
+                                          const float *llr, int32_t n_frames, float *z_out, void *workspace,
+                                          size_t ws_bytes, void *stream);
+
+/* Mean binary cross-entropy of the soft decisions sigma(-Z^(K)) (probability
+ * that a bit is 1) against the transmitted bits, over all n_frames x n_vars
+ * bits, after ldpc_learned_forward.  target_bits: device [n_frames][ceil(N/8)]
+ * packed like hard_bits, or NULL for the all-zero codeword.  loss: device
+ * float scalar.  want_grad != 0 also leaves dLoss/dZ^(K) in the workspace for
+ * ldpc_learned_backward(dz = NULL).  The sum is reduced in a fixed order. */
+LDPC_API ldpc_status ldpc_learned_loss(const ldpc_code *code, int32_t n_iters, int32_t n_frames,
+                                       const uint8_t *target_bits, float *loss, int32_t want_grad,
+                                       void *workspace, size_t ws_bytes, void *stream);
+
+/* Backward (adjoint) through the unrolled iterations: dbeta (device,
+ * [n_iters][n_classes]) = sum over frames of dLoss/dbeta for the gradient dz
+ * (device [n_frames][n_vars] float32 = dLoss/dZ^(K), or NULL to use the one
+ * ldpc_learned_loss left in the workspace).  Each iteration's row reduction is
+ * recomputed from the checkpoints; the minimum is differentiated through its
+ * argument (lowest position on ties, sgn(0) = +1), the offset through
+ * [min > beta].  Deterministic: no floating-point atomics touch dbeta. */
+LDPC_API ldpc_status ldpc_learned_backward(const ldpc_code *code, int32_t n_iters, const float *beta,
+                                           const float *dz, int32_t n_frames, float *dbeta, void *workspace,
+                                           size_t ws_bytes, void *stream);
+
+/* One Adam step (Kingma & Ba, 2015) on n float32 parameters, all device
+ * buffers: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps); step >= 1. */
+LDPC_API ldpc_status ldpc_adam_step(float *params, const float *grads, float *m, float *v, int32_t n,
+                                    int32_t step, float lr, float beta1, float beta2, float eps, void *stream);
+
+/* BPSK over AWGN channel values on the device (Section II): y = (1 - 2 x) +
+ * sigma xi, LLR = 2 y / sigma^2, sigma^2 = 1 / (2 rate 10^(EbN0/10)).  Frame f
+ * (global index first_frame + f) draws its Eb/N0 uniformly in [ebn0_lo_db,
+ * ebn0_hi_db] and its noise from Philox4x32-10 keyed by seed (Salmon et al.,
+ * SC 2011; counter (g, frame, 0) gives the Box-Muller normals of variables
+ * 4g..4g+3, counter (2^32-1, frame, 1) the Eb/N0 draw).  codewords: device
+ * [n_frames][ceil(n_vars/8)] packed bits, or NULL for all-zero.  llr: device
+ * [n_frames][n_vars] float32; ebn0_out: device [n_frames] or NULL. */
+LDPC_API ldpc_status ldpc_awgn_llr_f32(int32_t n_vars, uint64_t seed, uint64_t first_frame, int32_t n_frames,
+                                       float ebn0_lo_db, float ebn0_hi_db, float rate, const uint8_t *codewords,
+                                       float *llr, float *ebn0_out, void *stream);
+
+/* q[i] = clamp(round_half_away(llr[i] / delta), -qc, qc) as int8 (the fixed-
+ * point channel input of ldpc_decode_batch); device buffers of n elements. */
+LDPC_API ldpc_status ldpc_quantize_llr(const float *llr, int64_t n, float delta, int32_t qc, int8_t *q,
+                                       void *stream);
+
 /* Size of the device scratch array built into the library for
  * ldpc_decode_batch_noalloc (held on every GPU that loads the library). */
 #define LDPC_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)

@@ -166,3 +166,30 @@ def decode_f64(code, q0, *, form="ss_1bit", rule="normalized", offset=0.0, lam=0
     if want_margin:
         r["margin"] = mg
     return r
+
+
+def learned_grad(code, q0, beta_tab, *, targets=None, threads=0):
+    """FP64 loss (sum over frames and bits of the BCE terms) and its gradient
+    w.r.t. beta_tab [K, M] for the learned offset decoder; also each frame's
+    distance ``gap`` to the nearest non-differentiable point."""
+    lib = _load()
+    if not hasattr(lib, "_lg_ready"):
+        P = ctypes.c_void_p
+        lib.orc_learned_grad_f64.argtypes = [P, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P, P, ctypes.c_int32]
+        lib.orc_learned_grad_f64.restype = ctypes.c_int
+        lib._lg_ready = True
+    q = np.ascontiguousarray(np.atleast_2d(q0), dtype=np.float64)
+    F, N = q.shape
+    bt = np.ascontiguousarray(beta_tab, dtype=np.float64)
+    K, M = bt.shape
+    c, keep = _code_struct(code.row_ptr, code.col_idx, code.n_vars)
+    assert keep[0].size - 1 == M and N == code.n_vars
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.uint8)
+    loss = np.zeros(1, np.float64)
+    db = np.zeros((K, M), np.float64)
+    gap = np.zeros(F, np.float64)
+    rc = lib.orc_learned_grad_f64(ctypes.byref(c), K, _ptr(bt), _ptr(q), _ptr(tg), F, _ptr(loss), _ptr(db),
+                                  _ptr(gap), int(threads))
+    if rc != 0:
+        raise ValueError("orc_learned_grad_f64 rejected its arguments")
+    return float(loss[0]), db, gap

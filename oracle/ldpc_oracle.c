@@ -485,3 +485,157 @@ int orc_decode_f64_margin(const orc_code *code, const orc_dparams *p, int32_t fo
   proto.margin_out = margin_out;
   return run_all(&proto, n_frames, n_threads);
 }
+
+/* --------------------------------------------------- learned offsets (FP64) */
+
+typedef struct {
+  const orc_code *c;
+  int32_t K;
+  const double *beta;
+  const double *q0;
+  const uint8_t *tg;
+  int32_t f0, f1;
+  double loss;
+  double *dbeta; /* [K][M], this thread's sum */
+  double *gap;
+  int err;
+} ljob;
+
+static double softplus(double x) { return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
+static double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+static void *run_ljob(void *arg) {
+  ljob *jb = (ljob *)arg;
+  const orc_code *c = jb->c;
+  const int32_t N = c->n_vars, M = c->n_checks, E = c->row_ptr[M], K = jb->K;
+  const int32_t *rp = c->row_ptr, *ci = c->col_idx;
+  /* forward record: u[k-1][e] (k = 1..K), L[k][e] (k = 0..K), Z[k][n] (k = 0..K) */
+  double *u = malloc(sizeof(double) * (size_t)K * E);
+  double *L = malloc(sizeof(double) * (size_t)(K + 1) * E);
+  double *Z = malloc(sizeof(double) * (size_t)(K + 1) * N);
+  double *gZ = malloc(sizeof(double) * (size_t)N);   /* dLoss/dZ^(k) */
+  double *gZp = malloc(sizeof(double) * (size_t)N);  /* dLoss/dZ^(k-1) */
+  double *gLx = malloc(sizeof(double) * (size_t)E);  /* dLoss/dL^(k) through u^(k+1) */
+  double *gL = malloc(sizeof(double) * (size_t)E);   /* total dLoss/dL^(k) */
+  double *gu = malloc(sizeof(double) * (size_t)E);   /* dLoss/du^(k) */
+  if (!u || !L || !Z || !gZ || !gZp || !gLx || !gL || !gu) { jb->err = -1; goto done; }
+  for (int32_t f = jb->f0; f < jb->f1; ++f) {
+    const double *q = jb->q0 + (size_t)f * N;
+    double g = INFINITY;
+    /* forward: Eq. (3) with the per-iteration, per-check offset */
+    for (int32_t e = 0; e < E; ++e) L[e] = 0.0; /* L^(0) = 0 */
+    for (int32_t n = 0; n < N; ++n) Z[n] = q[n];
+    for (int32_t k = 1; k <= K; ++k) {
+      double *uk = u + (size_t)(k - 1) * E, *Lk = L + (size_t)k * E, *Lp = L + (size_t)(k - 1) * E;
+      double *Zk = Z + (size_t)k * N, *Zp = Z + (size_t)(k - 1) * N;
+      for (int32_t n = 0; n < N; ++n) Zk[n] = q[n];
+      for (int32_t m = 0; m < M; ++m) {
+        const double bt = jb->beta[(size_t)(k - 1) * M + m];
+        const int32_t d = rp[m + 1] - rp[m];
+        for (int32_t j = 0; j < d; ++j) uk[rp[m] + j] = Zp[ci[rp[m] + j]] - Lp[rp[m] + j];
+        double a1 = INFINITY, a2 = INFINITY;
+        for (int32_t j = 0; j < d; ++j) {
+          const double a = fabs(uk[rp[m] + j]);
+          if (a < g) g = a;
+          if (a < a1) { a2 = a1; a1 = a; } else if (a < a2) a2 = a;
+        }
+        if (a2 - a1 < g) g = a2 - a1;
+        if (fabs(a1 - bt) < g) g = fabs(a1 - bt);
+        if (fabs(a2 - bt) < g) g = fabs(a2 - bt);
+        for (int32_t j = 0; j < d; ++j) {
+          double sg = 1.0, mn = INFINITY;
+          for (int32_t t = 0; t < d; ++t) {
+            if (t == j) continue;
+            const double v = uk[rp[m] + t];
+            sg *= (v > 0) - (v < 0);
+            if (fabs(v) < mn) mn = fabs(v);
+          }
+          const double l = sg * (mn > bt ? mn - bt : 0.0);
+          Lk[rp[m] + j] = l;
+          Zk[ci[rp[m] + j]] += l;
+        }
+      }
+    }
+    /* loss and dLoss/dZ^(K) */
+    const double *ZK = Z + (size_t)K * N;
+    for (int32_t n = 0; n < N; ++n) {
+      const int t = jb->tg ? jb->tg[(size_t)f * N + n] : 0;
+      jb->loss += softplus(t ? ZK[n] : -ZK[n]);
+      gZ[n] = t ? sigm(ZK[n]) : sigm(ZK[n]) - 1.0;
+    }
+    for (int32_t e = 0; e < E; ++e) gLx[e] = 0.0;
+    /* reverse sweep over the iterations */
+    for (int32_t k = K; k >= 1; --k) {
+      const double *uk = u + (size_t)(k - 1) * E;
+      /* Z^(k) = Z0 + sum_m L^(k): every message receives its variable's gradient */
+      for (int32_t e = 0; e < E; ++e) { gL[e] = gZ[ci[e]] + gLx[e]; gu[e] = 0.0; }
+      for (int32_t m = 0; m < M; ++m) {
+        const double bt = jb->beta[(size_t)(k - 1) * M + m];
+        const int32_t d = rp[m + 1] - rp[m];
+        for (int32_t j = 0; j < d; ++j) {
+          double sg = 1.0, mn = INFINITY;
+          int32_t arg = -1;
+          for (int32_t t = 0; t < d; ++t) {
+            if (t == j) continue;
+            const double v = uk[rp[m] + t];
+            sg *= (v > 0) - (v < 0);
+            if (fabs(v) < mn) { mn = fabs(v); arg = t; }
+          }
+          if (!(mn > bt)) continue; /* the offset's max(., 0) is inactive */
+          const double gl = gL[rp[m] + j];
+          jb->dbeta[(size_t)(k - 1) * M + m] -= gl * sg;          /* dL/dbeta = -sg */
+          const double v = uk[rp[m] + arg];
+          gu[rp[m] + arg] += gl * sg * (v < 0 ? -1.0 : 1.0);      /* dL/du_arg = sg sgn(u_arg) */
+        }
+      }
+      /* u^(k)_e = Z^(k-1)_n - L^(k-1)_e */
+      for (int32_t n = 0; n < N; ++n) gZp[n] = 0.0;
+      for (int32_t e = 0; e < E; ++e) { gZp[ci[e]] += gu[e]; gLx[e] = -gu[e]; }
+      for (int32_t n = 0; n < N; ++n) gZ[n] = gZp[n];
+    }
+    if (jb->gap) jb->gap[f] = g;
+  }
+done:
+  free(u); free(L); free(Z); free(gZ); free(gZp); free(gLx); free(gL); free(gu);
+  return NULL;
+}
+
+int orc_learned_grad_f64(const orc_code *code, int32_t n_iters, const double *beta_tab, const double *q0,
+                         const uint8_t *targets, int32_t n_frames, double *loss_sum, double *dbeta,
+                         double *gap, int32_t n_threads) {
+  if (validate(code, ORC_SS_FIXED) || n_iters < 1 || !beta_tab || !q0 || n_frames < 0 || !loss_sum || !dbeta)
+    return -1;
+  const int32_t M = code->n_checks;
+  const size_t nb = (size_t)n_iters * M;
+  for (size_t i = 0; i < nb; ++i) dbeta[i] = 0.0;
+  *loss_sum = 0.0;
+  if (n_frames == 0) return 0;
+  if (n_threads <= 0) n_threads = orc_default_threads();
+  if (n_threads > n_frames) n_threads = n_frames;
+  ljob *jobs = (ljob *)calloc((size_t)n_threads, sizeof(ljob));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  int err = (!jobs || !th) ? -1 : 0;
+  int32_t started = 0;
+  for (int32_t i = 0; i < n_threads && !err; ++i) {
+    jobs[i].c = code; jobs[i].K = n_iters; jobs[i].beta = beta_tab; jobs[i].q0 = q0; jobs[i].tg = targets;
+    jobs[i].f0 = (int32_t)((int64_t)n_frames * i / n_threads);
+    jobs[i].f1 = (int32_t)((int64_t)n_frames * (i + 1) / n_threads);
+    jobs[i].gap = gap;
+    jobs[i].dbeta = (double *)calloc(nb, sizeof(double));
+    if (!jobs[i].dbeta) { err = -1; break; }
+    if (pthread_create(&th[i], NULL, run_ljob, &jobs[i])) err = -1;
+    else started++;
+  }
+  for (int32_t i = 0; i < started; ++i) {
+    pthread_join(th[i], NULL);
+    if (jobs[i].err) err = -1;
+  }
+  /* sum in thread order (each thread's frames in order): deterministic */
+  for (int32_t i = 0; i < started && !err; ++i) {
+    *loss_sum += jobs[i].loss;
+    for (size_t t = 0; t < nb; ++t) dbeta[t] += jobs[i].dbeta[t];
+  }
+  for (int32_t i = 0; i < n_threads; ++i) free(jobs ? jobs[i].dbeta : NULL);
+  free(jobs); free(th);
+  return err;
+}

@@ -92,6 +92,22 @@ int orc_decode_f64_margin(const orc_code *code, const orc_dparams *p, int32_t fo
                           uint8_t *ok, double *z_out, double *l_out, double *margin_out,
                           int32_t n_threads);
 
+/* Learned offset min-sum (offset beta per iteration and check), FP64 reference
+   of the loss and its gradient.  Runs n_iters iterations of Eq. (3) without
+   early stop, with |L| <- max(|L| - beta_tab[k-1][m], 0), then the mean-free
+   binary cross-entropy sum over bits of softplus(-Z) (bit 0) / softplus(Z)
+   (bit 1) of the final posterior; targets [F][N] (0/1, nullable = all zero).
+   Reverse mode through every message, each message differentiated literally:
+   L_j = prod_{j'!=j} sgn(u_j') * max(min_{j'!=j} |u_j'| - beta, 0), the minimum
+   through its lowest-position argument, sgn(0) = +1 for the derivative of
+   |u|.  Outputs: loss_sum (sum over frames and bits), dbeta [n_iters][M]
+   (gradient of loss_sum), gap [F] (nullable): the frame's smallest distance to
+   a point where the loss is not differentiable -- over every iteration and
+   check, min2 - min1 of |u|, |min1 - beta|, |min2 - beta| and the smallest |u|. */
+int orc_learned_grad_f64(const orc_code *code, int32_t n_iters, const double *beta_tab, const double *q0,
+                         const uint8_t *targets, int32_t n_frames, double *loss_sum, double *dbeta,
+                         double *gap, int32_t n_threads);
+
 /* Number of threads orc_decode_* would use for n_threads <= 0. */
 int32_t orc_default_threads(void);
 

@@ -22,6 +22,9 @@ struct ldpc_code {
   uint8_t* d_rdeg = nullptr;
   int32_t* d_cptr = nullptr;
   int32_t* d_cslot = nullptr;
+  uint8_t* d_rclass = nullptr;      // degree class of every check
+  int32_t n_classes = 0;
+  int32_t class_deg[32] = {};       // check degree of each class, ascending
   int32_t ell_w = 0;
   int sm_count = 0;
   size_t smem_optin = 0;
@@ -216,6 +219,15 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   std::vector<uint16_t> ell16(narrow ? (size_t)max_row * n_checks : 0);
   std::vector<int32_t> ell32(narrow ? 0 : (size_t)max_row * n_checks);
   std::vector<uint8_t> rdeg((size_t)n_checks);
+  // degree classes: the distinct check degrees, ascending
+  int32_t n_cls = 0, cls_deg[32] = {};
+  for (int32_t dgr = 2; dgr <= 32; ++dgr)
+    for (int32_t m = 0; m < n_checks; ++m)
+      if (row_ptr[m + 1] - row_ptr[m] == dgr) { cls_deg[n_cls++] = dgr; break; }
+  std::vector<uint8_t> rclass((size_t)n_checks);
+  for (int32_t m = 0; m < n_checks; ++m)
+    for (int32_t q = 0; q < n_cls; ++q)
+      if (cls_deg[q] == row_ptr[m + 1] - row_ptr[m]) rclass[(size_t)m] = (uint8_t)q;
   // variable -> edge slots (j * M + m), in increasing m, for the two-scan comparator
   std::vector<int32_t> cptr((size_t)n_vars + 1, 0), cslot((size_t)E), cfill((size_t)n_vars, 0);
   for (int32_t e = 0; e < E; ++e) cptr[(size_t)col_idx[e] + 1]++;
@@ -250,6 +262,8 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   c->max_row_deg = max_row;
   c->max_col_deg = max_col;
   c->ell_w = max_row;
+  c->n_classes = n_cls;
+  for (int32_t q = 0; q < n_cls; ++q) c->class_deg[q] = cls_deg[q];
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
   c->sm_count = v;
@@ -266,6 +280,8 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
       (err = cudaMalloc(&c->d_cslot, sizeof(int32_t) * (size_t)E)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_cslot, cslot.data(), sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
+      (err = cudaMalloc(&c->d_rclass, (size_t)n_checks)) != cudaSuccess ||
+      (err = cudaMemcpy(c->d_rclass, rclass.data(), (size_t)n_checks, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMalloc(&c->d_rdeg, (size_t)n_checks)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_rdeg, rdeg.data(), (size_t)n_checks, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (narrow && (err = cudaMalloc(&c->d_ell16, sizeof(uint16_t) * ell16.size())) != cudaSuccess) ||
@@ -285,6 +301,7 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
     cudaFree(c->d_ell32);
     cudaFree(c->d_cptr);
     cudaFree(c->d_cslot);
+    cudaFree(c->d_rclass);
     delete c;
     return cuda_fail(err, "ldpc_code_create device copy");
   }
@@ -305,6 +322,7 @@ ldpc_status ldpc_code_destroy(ldpc_code* code) {
   cudaFree(code->d_ell32);
   cudaFree(code->d_cptr);
   cudaFree(code->d_cslot);
+  cudaFree(code->d_rclass);
   delete code;
   return LDPC_OK;
 }
@@ -398,6 +416,112 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
   }
   if (err != cudaSuccess) return cuda_fail(err, "ldpc_decode_batch launch");
   return LDPC_OK;
+}
+
+ldpc_status ldpc_code_degree_classes(const ldpc_code* code, int32_t* n_classes, int32_t* degrees) {
+  g_last_error.clear();
+  if (code == nullptr || n_classes == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code and n_classes must be non-NULL");
+  *n_classes = code->n_classes;
+  if (degrees != nullptr)
+    for (int32_t q = 0; q < code->n_classes; ++q) degrees[q] = code->class_deg[q];
+  return LDPC_OK;
+}
+
+namespace {
+constexpr int kLearnedMaxClasses = 4;
+
+ldpc_status learned_check(const ldpc_code* code, int32_t n_iters, int32_t n_frames, void* ws, size_t ws_bytes,
+                          ldpc::LearnedLayout* L) {
+  if (code == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code is NULL");
+  if (n_iters < 1 || n_iters > 64) return fail(LDPC_ERR_INVALID_ARG, "n_iters %d outside [1, 64]", n_iters);
+  if (n_frames < 1) return fail(LDPC_ERR_INVALID_ARG, "n_frames %d < 1", n_frames);
+  if (code->n_classes > kLearnedMaxClasses)
+    return fail(LDPC_ERR_UNSUPPORTED, "learned offsets support at most %d check-degree classes, the code has %d",
+                kLearnedMaxClasses, code->n_classes);
+  *L = ldpc::learned_layout(code->N, code->M, n_iters, code->n_classes, n_frames);
+  if (ws == nullptr || ws_bytes < L->total)
+    return fail(LDPC_ERR_INVALID_ARG, "learned workspace of %zu bytes needed, %zu given", L->total,
+                ws ? ws_bytes : (size_t)0);
+  if (((uintptr_t)ws & 255u) != 0) return fail(LDPC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  return LDPC_OK;
+}
+}  // namespace
+
+ldpc_status ldpc_learned_workspace_size(const ldpc_code* code, int32_t n_iters, int32_t n_frames, size_t* bytes) {
+  g_last_error.clear();
+  if (code == nullptr || bytes == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code and bytes must be non-NULL");
+  if (n_iters < 1 || n_frames < 1) return fail(LDPC_ERR_INVALID_ARG, "n_iters and n_frames must be >= 1");
+  *bytes = ldpc::learned_layout(code->N, code->M, n_iters, code->n_classes, n_frames).total;
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_learned_forward(const ldpc_code* code, int32_t n_iters, const float* beta, const float* llr,
+                                 int32_t n_frames, float* z_out, void* workspace, size_t ws_bytes, void* stream) {
+  g_last_error.clear();
+  ldpc::LearnedLayout L;
+  ldpc_status s = learned_check(code, n_iters, n_frames, workspace, ws_bytes, &L);
+  if (s != LDPC_OK) return s;
+  if (beta == nullptr || llr == nullptr) return fail(LDPC_ERR_INVALID_ARG, "beta and llr must be non-NULL");
+  DeviceGuard guard(code->device);
+  const cudaError_t e = ldpc::learned_forward(view(code), code->d_rclass, code->n_classes, n_iters, beta, L,
+                                              workspace, llr, n_frames, z_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_learned_forward launch");
+}
+
+ldpc_status ldpc_learned_loss(const ldpc_code* code, int32_t n_iters, int32_t n_frames, const uint8_t* target_bits,
+                              float* loss, int32_t want_grad, void* workspace, size_t ws_bytes, void* stream) {
+  g_last_error.clear();
+  ldpc::LearnedLayout L;
+  ldpc_status s = learned_check(code, n_iters, n_frames, workspace, ws_bytes, &L);
+  if (s != LDPC_OK) return s;
+  if (loss == nullptr) return fail(LDPC_ERR_INVALID_ARG, "loss must be non-NULL");
+  DeviceGuard guard(code->device);
+  const cudaError_t e = ldpc::learned_bce(view(code), code->n_classes, n_iters, L, workspace, n_frames, target_bits,
+                                          loss, want_grad != 0, (cudaStream_t)stream);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_learned_loss launch");
+}
+
+ldpc_status ldpc_learned_backward(const ldpc_code* code, int32_t n_iters, const float* beta, const float* dz,
+                                  int32_t n_frames, float* dbeta, void* workspace, size_t ws_bytes, void* stream) {
+  g_last_error.clear();
+  ldpc::LearnedLayout L;
+  ldpc_status s = learned_check(code, n_iters, n_frames, workspace, ws_bytes, &L);
+  if (s != LDPC_OK) return s;
+  if (beta == nullptr || dbeta == nullptr) return fail(LDPC_ERR_INVALID_ARG, "beta and dbeta must be non-NULL");
+  DeviceGuard guard(code->device);
+  const cudaError_t e = ldpc::learned_backward(view(code), code->d_rclass, code->n_classes, n_iters, beta, L,
+                                               workspace, dz, n_frames, dbeta, (cudaStream_t)stream);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_learned_backward launch");
+}
+
+ldpc_status ldpc_adam_step(float* params, const float* grads, float* m, float* v, int32_t n, int32_t step, float lr,
+                           float beta1, float beta2, float eps, void* stream) {
+  g_last_error.clear();
+  if (params == nullptr || grads == nullptr || m == nullptr || v == nullptr || n < 1 || step < 1)
+    return fail(LDPC_ERR_INVALID_ARG, "adam: non-NULL buffers, n >= 1 and step >= 1 required");
+  const cudaError_t e = ldpc::adam_step(params, grads, m, v, n, step, lr, beta1, beta2, eps, (cudaStream_t)stream);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_adam_step launch");
+}
+
+ldpc_status ldpc_awgn_llr_f32(int32_t n_vars, uint64_t seed, uint64_t first_frame, int32_t n_frames, float ebn0_lo_db,
+                              float ebn0_hi_db, float rate, const uint8_t* codewords, float* llr, float* ebn0_out,
+                              void* stream) {
+  g_last_error.clear();
+  if (n_vars < 1 || n_frames < 0 || llr == nullptr || !(rate > 0.0f && rate <= 1.0f) || ebn0_hi_db < ebn0_lo_db)
+    return fail(LDPC_ERR_INVALID_ARG, "awgn: n_vars >= 1, llr non-NULL, 0 < rate <= 1, lo <= hi required");
+  if (n_frames == 0) return LDPC_OK;
+  const cudaError_t e = ldpc::awgn_llr(n_vars, seed, first_frame, n_frames, ebn0_lo_db, ebn0_hi_db, rate, codewords,
+                                       llr, ebn0_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_awgn_llr_f32 launch");
+}
+
+ldpc_status ldpc_quantize_llr(const float* llr, int64_t n, float delta, int32_t qc, int8_t* q, void* stream) {
+  g_last_error.clear();
+  if (llr == nullptr || q == nullptr || n < 0 || !(delta > 0.0f) || qc < 1 || qc > 127)
+    return fail(LDPC_ERR_INVALID_ARG, "quantize: non-NULL buffers, delta > 0, 1 <= qc <= 127 required");
+  if (n == 0) return LDPC_OK;
+  const cudaError_t e = ldpc::quantize_llr(llr, (size_t)n, delta, qc, q, (cudaStream_t)stream);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_quantize_llr launch");
 }
 
 // ---------------------------------------------------------------------------

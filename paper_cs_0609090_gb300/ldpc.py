@@ -33,7 +33,9 @@ KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onch
 
 # Every symbol include/ldpc_gb300.h declares.
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",
-           "ldpc_decode_batch", "ldpc_decode_batch_noalloc", "ldpc_last_error")
+           "ldpc_decode_batch", "ldpc_decode_batch_noalloc", "ldpc_code_degree_classes",
+           "ldpc_learned_workspace_size", "ldpc_learned_forward", "ldpc_learned_loss", "ldpc_learned_backward",
+           "ldpc_adam_step", "ldpc_awgn_llr_f32", "ldpc_quantize_llr", "ldpc_last_error")
 NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -61,6 +63,17 @@ _lib.ldpc_decode_batch.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), _P, c
                                    _P, _P, ctypes.c_size_t, _P]
 _lib.ldpc_decode_batch_noalloc.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), _P, ctypes.c_int32, _P, _P,
                                            _P, _P, _P]
+_lib.ldpc_code_degree_classes.argtypes = [_P, _P, _P]
+_lib.ldpc_learned_workspace_size.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+_lib.ldpc_learned_forward.argtypes = [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P]
+_lib.ldpc_learned_loss.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t,
+                                   _P]
+_lib.ldpc_learned_backward.argtypes = [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P]
+_lib.ldpc_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, _P]
+_lib.ldpc_awgn_llr_f32.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]
+_lib.ldpc_quantize_llr.argtypes = [_P, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, _P, _P]
 _lib.ldpc_last_error.restype = ctypes.c_char_p
 for _f in EXPORTS[:-1]:
     getattr(_lib, _f).restype = ctypes.c_int32
@@ -152,6 +165,58 @@ def ldpc_decode_batch_noalloc(code: int, params: ldpc_decode_params, llr, n_fram
     _check(_lib.ldpc_decode_batch_noalloc(_P(code), ctypes.byref(params), _ptr(llr), int(n_frames), _ptr(hard_bits),
                                           _ptr(iters_used), _ptr(syndrome_ok), _ptr(llr_out),
                                           _stream_handle(stream)), "ldpc_decode_batch_noalloc")
+
+
+def ldpc_code_degree_classes(code: int) -> list:
+    n = ctypes.c_int32()
+    deg = (ctypes.c_int32 * 32)()
+    _check(_lib.ldpc_code_degree_classes(_P(code), ctypes.byref(n), deg), "ldpc_code_degree_classes")
+    return [deg[i] for i in range(n.value)]
+
+
+def ldpc_learned_workspace_size(code: int, n_iters: int, n_frames: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib.ldpc_learned_workspace_size(_P(code), int(n_iters), int(n_frames), ctypes.byref(out)),
+           "ldpc_learned_workspace_size")
+    return out.value
+
+
+def ldpc_learned_forward(code: int, n_iters: int, beta, llr, n_frames: int, z_out, workspace, ws_bytes: int,
+                         stream=None) -> None:
+    _check(_lib.ldpc_learned_forward(_P(code), int(n_iters), _ptr(beta), _ptr(llr), int(n_frames), _ptr(z_out),
+                                     _ptr(workspace), int(ws_bytes), _stream_handle(stream)), "ldpc_learned_forward")
+
+
+def ldpc_learned_loss(code: int, n_iters: int, n_frames: int, target_bits, loss, want_grad: bool, workspace,
+                      ws_bytes: int, stream=None) -> None:
+    _check(_lib.ldpc_learned_loss(_P(code), int(n_iters), int(n_frames), _ptr(target_bits), _ptr(loss),
+                                  int(bool(want_grad)), _ptr(workspace), int(ws_bytes), _stream_handle(stream)),
+           "ldpc_learned_loss")
+
+
+def ldpc_learned_backward(code: int, n_iters: int, beta, dz, n_frames: int, dbeta, workspace, ws_bytes: int,
+                          stream=None) -> None:
+    _check(_lib.ldpc_learned_backward(_P(code), int(n_iters), _ptr(beta), _ptr(dz), int(n_frames), _ptr(dbeta),
+                                      _ptr(workspace), int(ws_bytes), _stream_handle(stream)),
+           "ldpc_learned_backward")
+
+
+def ldpc_adam_step(params, grads, m, v, n: int, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                   eps: float = 1e-8, stream=None) -> None:
+    _check(_lib.ldpc_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(n), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps), _stream_handle(stream)), "ldpc_adam_step")
+
+
+def ldpc_awgn_llr_f32(n_vars: int, seed: int, first_frame: int, n_frames: int, ebn0_lo_db: float,
+                      ebn0_hi_db: float, rate: float, codewords, llr, ebn0_out=None, stream=None) -> None:
+    _check(_lib.ldpc_awgn_llr_f32(int(n_vars), int(seed), int(first_frame), int(n_frames), float(ebn0_lo_db),
+                                  float(ebn0_hi_db), float(rate), _ptr(codewords), _ptr(llr), _ptr(ebn0_out),
+                                  _stream_handle(stream)), "ldpc_awgn_llr_f32")
+
+
+def ldpc_quantize_llr(llr, n: int, delta: float, qc: int, q, stream=None) -> None:
+    _check(_lib.ldpc_quantize_llr(_ptr(llr), int(n), float(delta), int(qc), _ptr(q), _stream_handle(stream)),
+           "ldpc_quantize_llr")
 
 
 class Code:
