@@ -11,12 +11,13 @@ struct DevCode {
   const int32_t* __restrict__ rp;  // [M+1]
   const int32_t* __restrict__ ci;  // [E]
   const int32_t* __restrict__ cdeg;  // [N] number of checks of each variable, |M(n)|
-  // The same adjacency transposed to edge-slot-major order for coalesced loads:
-  // variable of position j of check m at ell[j * M + m] (j < ell_w, padded with
-  // the check's last variable); uint16 when N <= 65535, else int32.
+  // The same adjacency transposed to edge-slot-major order for coalesced loads,
+  // with the checks in an internal order sorted by degree: variable of position j
+  // of internal check i at ell[j * M + i] (j < ell_w, padded with the check's last
+  // variable); uint16 when N <= 65535, else int32.
   const uint16_t* __restrict__ ell16;
   const int32_t* __restrict__ ell32;
-  const uint8_t* __restrict__ rdeg;  // [M] check degrees |N(m)|
+  const uint8_t* __restrict__ rdeg;  // [M] degrees |N(m)| in the internal check order
   int32_t ell_w;
   // Variable->check adjacency M(n) for the two-scan comparator only: the edge
   // slots (j * M + m) of variable n are cslot[cptr[n] .. cptr[n+1]-1].

@@ -35,7 +35,7 @@ cudaError_t onchip_int8_launch(const DevCode& c, const IntRule& r, int form, con
                                int16_t* zout, cudaStream_t stream);
 
 // Packed binary16 variant (two frames per instruction, exact for integers < 2048).
-bool onchip_h2_eligible(int n_vars, int max_row_deg, int max_col_deg, int qm);
+bool onchip_h2_eligible(int n_vars, int max_row_deg, int max_col_deg, int qm, int rule, int num);
 bool onchip_h2_plan(const DevCode& c, int form, int32_t n_frames, int sm_count, size_t smem_optin,
                     int max_row_deg, OnchipPlan* plan);
 // Sets plan.grid from occupancy; launches unless occupancy_only.

@@ -1,5 +1,6 @@
 // ldpc_api.cu -- the C ABI (include/ldpc_gb300.h): argument checks, the device
 // copy of a code, kernel selection and error reporting.  No kernel logic here.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -132,7 +133,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     const bool want_half = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF;
     const bool want_int = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_INT;
     const bool want_stream = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM;
-    if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat) &&
+    if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num) &&
         ldpc::onchip_h2_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_H2;
       ch->ws = 0;
@@ -155,7 +156,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
   }
   if (p->dtype == LDPC_DTYPE_INT8 && p->form == LDPC_FORM_TWO_SCAN) {
     if ((p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF) &&
-        ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat) &&
+        ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num) &&
         ldpc::onchip_twoscan_plan(v, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_TWOSCAN;
       ch->ws = 0;
@@ -228,22 +229,33 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   for (int32_t m = 0; m < n_checks; ++m)
     for (int32_t q = 0; q < n_cls; ++q)
       if (cls_deg[q] == row_ptr[m + 1] - row_ptr[m]) rclass[(size_t)m] = (uint8_t)q;
-  // variable -> edge slots (j * M + m), in increasing m, for the two-scan comparator
+  // The frame-resident kernels visit checks in an internal order sorted by degree
+  // (stable), so that the checks of a warp share one degree; check order does not
+  // change any result (each check's messages depend only on the previous
+  // iteration, and the exact integer sums do not depend on the order).
+  std::vector<int32_t> order((size_t)n_checks), pos((size_t)n_checks);
+  for (int32_t m = 0; m < n_checks; ++m) order[(size_t)m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return row_ptr[a + 1] - row_ptr[a] < row_ptr[b + 1] - row_ptr[b];
+  });
+  for (int32_t i = 0; i < n_checks; ++i) pos[(size_t)order[(size_t)i]] = i;
+  // variable -> edge slots (j * M + internal check index), for the two-scan comparator
   std::vector<int32_t> cptr((size_t)n_vars + 1, 0), cslot((size_t)E), cfill((size_t)n_vars, 0);
   for (int32_t e = 0; e < E; ++e) cptr[(size_t)col_idx[e] + 1]++;
   for (int32_t n = 0; n < n_vars; ++n) cptr[(size_t)n + 1] += cptr[(size_t)n];
   for (int32_t m = 0; m < n_checks; ++m)
     for (int32_t j = 0; j < row_ptr[m + 1] - row_ptr[m]; ++j) {
       const int32_t n = col_idx[row_ptr[m] + j];
-      cslot[(size_t)(cptr[(size_t)n] + cfill[(size_t)n]++)] = j * n_checks + m;
+      cslot[(size_t)(cptr[(size_t)n] + cfill[(size_t)n]++)] = j * n_checks + pos[(size_t)m];
     }
-  for (int32_t m = 0; m < n_checks; ++m) {
+  for (int32_t i = 0; i < n_checks; ++i) {
+    const int32_t m = order[(size_t)i];
     const int32_t d = row_ptr[m + 1] - row_ptr[m];
-    rdeg[(size_t)m] = (uint8_t)d;
+    rdeg[(size_t)i] = (uint8_t)d;
     for (int32_t j = 0; j < max_row; ++j) {
       const int32_t n = col_idx[row_ptr[m] + (j < d ? j : d - 1)];
-      if (narrow) ell16[(size_t)j * n_checks + m] = (uint16_t)n;
-      else ell32[(size_t)j * n_checks + m] = n;
+      if (narrow) ell16[(size_t)j * n_checks + i] = (uint16_t)n;
+      else ell32[(size_t)j * n_checks + i] = n;
     }
   }
 

@@ -15,8 +15,11 @@
 //   Acc  [N][P]  i32    Z^(k) as the integer lo + 65536 hi; every message adds the
 //                       bit pattern of (L + 1536) per lane, i.e. 0x6600 + L, and
 //                       the resets subtract col_degree(n) * 0x66006600
-//   form 1 (Section V): [M][P] {A, B, n~ as half2; signs: frame lo bits 0-15,
-//                       frame hi bits 16-31}
+//   form 1 (Section V): [M][P] {A, B, n~ as half2; signs, bit-reversed: the
+//                       sign of position j of the even frame at bit 15 - j, of
+//                       the odd frame at bit 31 - j, so that shifting the word
+//                       left by j (a running S + S) brings both to the binary16
+//                       sign bits}
 //   form 0 (Section IV): [E][P] u16: L + 128 per frame (one byte each)
 #include <cuda_fp16.h>
 
@@ -63,23 +66,30 @@ __device__ __forceinline__ void st_pairs(uint32_t* __restrict__ Zs, int n, const
 }
 
 // Column of position j of check m: from the shared-memory copy or from global.
+// Column of position j of internal check m: shared-memory copy or global table.
 template <bool SIDX>
 __device__ __forceinline__ int colj(const DevCode& c, const uint16_t* __restrict__ sidx, int j, int m) {
-  if constexpr (SIDX) return (int)sidx[(size_t)j * c.M + m];
-  else return (int)__ldg(c.ell16 + (size_t)j * c.M + m);
+  if constexpr (SIDX) return (int)sidx[j * c.M + m];
+  else return (int)__ldg(c.ell16 + j * c.M + m);
 }
 
-template <int G, int DMAX, bool SIDX>
-__device__ __forceinline__ uint32_t row_parity_h2(const DevCode& c, const uint16_t* __restrict__ sidx,
-                                                  const uint32_t* __restrict__ Zs, int m) {
+// |x| of both halves (an operand modifier of the instruction that consumes it).
+__device__ __forceinline__ uint32_t hab(uint32_t a) {
+  uint32_t d; asm("abs.f16x2 %0, %1;" : "=r"(d) : "r"(a)); return d;
+}
+
+// Decision parity of check m for the G frames (bit g set: unsatisfied).
+template <int G, int D, int DMAX, bool SIDX>
+__device__ __forceinline__ uint32_t row_parity_body(const DevCode& c, const uint16_t* __restrict__ sidx,
+                                                    const uint32_t* __restrict__ Zs, int m, int d) {
   constexpr int P = G / 2;
-  const int d = c.deg(m);
+  constexpr int NJ = D > 0 ? D : DMAX;
   uint32_t y[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) y[p] = 0;
 #pragma unroll
-  for (int j = 0; j < DMAX; ++j) {
-    if (j < d) {
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
       uint32_t w[P];
       ld_pairs<G>(Zs, colj<SIDX>(c, sidx, j, m), w);
 #pragma unroll
@@ -92,119 +102,168 @@ __device__ __forceinline__ uint32_t row_parity_h2(const DevCode& c, const uint16
   return par;
 }
 
-// One check m for all G frames: Eq. (3) with Section V state (FORM 1) or
-// per-edge messages (FORM 0).  Returns decision-parity bits of x^(k-1) when ES.
-template <int G, int FORM, int DMAX, bool ES, bool SIDX>
-__device__ __forceinline__ uint32_t check_update_h2(const DevCode& c, const IntRule& r, uint32_t qm2, int m,
-                                                    const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
-                                                    uint4* __restrict__ St, uint16_t* __restrict__ Lm,
-                                                    const uint16_t* __restrict__ sidx) {
-  constexpr int P = G / 2;
-  const int d = c.deg(m);
-  // per-edge messages (form 0) are stored edge-slot-major too: slot j of check m
-  // at Lm[j * M + m]
-  const int M = c.M;
+// Section III's magnitude rule without branches: g(x) = max((x - beta) num, 0)
+// >> shift (plain: beta 0, num 1, shift 0; offset: beta, 1, 0; normalized: 0,
+// num, shift), which floors the normalized magnitude like the integer rule.
+struct H2Rule {
+  int32_t beta, num, shift;
+  __device__ __forceinline__ int32_t g(int32_t x) const { return max((x - beta) * num, 0) >> shift; }
+};
+__device__ inline H2Rule make_h2rule(const IntRule& r) {
+  H2Rule h;
+  h.beta = r.rule == 1 ? r.beta : 0;
+  h.num = r.rule == 2 ? r.num : 1;
+  h.shift = r.rule == 2 ? r.shift : 0;
+  return h;
+}
 
-  uint32_t A2[P], D2[P], I2[P], S[P];
+// One check m for all G frames: Eq. (3) with the Section V state (FORM 1) or
+// per-edge messages (FORM 0).  D > 0: the check has exactly D positions (fully
+// unrolled); D == 0: d <= DMAX positions, guarded.  Returns the decision parity
+// bits of x^(k-1) when ES.
+template <int G, int FORM, int D, int DMAX, bool ES, bool SIDX>
+__device__ __forceinline__ uint32_t check_body(const DevCode& c, const H2Rule& rule, uint32_t qm2, int m, int d,
+                                               const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
+                                               uint4* __restrict__ St, uint16_t* __restrict__ Lm,
+                                               const uint16_t* __restrict__ sidx) {
+  constexpr int P = G / 2;
+  constexpr int NJ = D > 0 ? D : DMAX;
+  // one frame pair: the pass-1 column indices stay in registers for pass 2;
+  // two pairs need those registers for state and reload them
+  constexpr bool KEEP = (P == 1 && FORM == 1 && !ES);
+  const int M = c.M;
+  uint32_t A2[P], B2[P], I2[P], S[P];
   if constexpr (FORM == 1) {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      const uint4 s = St[(size_t)m * P + p];
+      const uint4 s = St[m * P + p];
       A2[p] = s.x;
-      D2[p] = hsub(s.y, s.x);
+      B2[p] = s.y;
       I2[p] = s.z;
       S[p] = s.w;
     }
   }
-  uint32_t K1[P], K2[P], X[P], NEG[P], Y[P];
+  uint32_t K1[P], K2[P], NEG[P], Y[P], SR[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     K1[p] = h2c(2048);
     K2[p] = h2c(2048);
-    X[p] = 0;
     NEG[p] = 0;
     Y[p] = 0;
+    if constexpr (FORM == 1) SR[p] = S[p];
   }
-
+  int col[KEEP ? NJ : 1];
 #pragma unroll
-  for (int j = 0; j < DMAX; ++j) {
-    if (j < d) {
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
       const int n = colj<SIDX>(c, sidx, j, m);
+      if constexpr (KEEP) col[j] = n;
       uint32_t w[P];
       ld_pairs<G>(Zs, n, w);
       uint32_t lv = 0;
       if constexpr (FORM == 0) {
-        if constexpr (P == 1) lv = Lm[(size_t)j * M + m];
-        else lv = reinterpret_cast<const uint32_t*>(Lm)[(size_t)j * M + m];
+        if constexpr (P == 1) lv = Lm[j * M + m];
+        else lv = reinterpret_cast<const uint32_t*>(Lm)[j * M + m];
       }
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         uint32_t L;
         if constexpr (FORM == 1) {
-          // f(A, B, n, n~): E = max(1 - |n~ - j|, 0) is 1 exactly at n~.
-          const uint32_t E = hfma_relu(habs(hsub(I2[p], h2c(j))), 0xBC00BC00u /* -1 */, h2c(1));
-          const uint32_t mag = hfma(D2[p], E, A2[p]);
-          L = mag ^ ((S[p] << (15 - j)) & 0x80008000u);
+          // f(A, B, n, n~) and the stored sign s_mn on the binary16 sign bit
+          const uint32_t msk = heq_mask(I2[p], h2c(j));
+          L = ((B2[p] & msk) | (A2[p] & ~msk)) ^ (SR[p] & 0x80008000u);
+          SR[p] += SR[p];
         } else {
           // byte L + 128 -> binary16 128 + (L + 128)/8 -> 8 h - 1152 = L
           const uint32_t b = (P == 1) ? lv : (lv >> (16 * p));
-          const uint32_t h = __byte_perm(b, 0x58u, 0x4140);
-          L = hfma(h, h2c(8), 0xE480E480u /* -1152 */);
+          L = hfma(__byte_perm(b, 0x58u, 0x4140), h2c(8), 0xE480E480u /* -1152 */);
         }
         const uint32_t u = hsub(w[p], L);
-        X[p] ^= u;
         if constexpr (ES) Y[p] ^= dec_bits(w[p]);
-        NEG[p] |= (u & 0x80008000u) >> (15 - j);
-        const uint32_t key = hfma(hmin(habs(u), qm2), h2c(16), h2c(j));
+        NEG[p] |= (u >> j) & (0x80008000u >> j);  // sign of u_j at bit 15 - j / 31 - j
+        const uint32_t key = hfma(hmin(hab(u), qm2), h2c(16), h2c(j));
         K2[p] = hmin(K2[p], hmax(K1[p], key));
         K1[p] = hmin(K1[p], key);
       }
     }
   }
 
-  const uint32_t dm = (d >= 16) ? 0xffffu : ((1u << d) - 1u);
+  const int dd = D > 0 ? D : d;
+  const uint32_t dlane = ((1u << dd) - 1u) << (16 - dd);  // bits 16-d .. 15
   uint32_t An[P], Bn[P], In[P], Sn[P];
   uint32_t par = 0;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     // sign of L^(k)_mj = parity of all input signs xor own sign
-    const uint32_t pm = prmt(X[p], 0u, 0xBB99u);  // 0xffff per frame with odd parity
-    Sn[p] = (NEG[p] ^ pm) & (dm | (dm << 16));
+    const uint32_t pm = ((__popc(NEG[p] & 0xffffu) & 1) ? 0x0000ffffu : 0u) |
+                        ((__popc(NEG[p] >> 16) & 1) ? 0xffff0000u : 0u);
+    Sn[p] = (NEG[p] ^ pm) & (dlane | (dlane << 16));
     const int32_t k1l = h_lo_int(K1[p]), k1h = h_hi_int(K1[p]);
     const int32_t k2l = h_lo_int(K2[p]), k2h = h_hi_int(K2[p]);
-    An[p] = small_to_h2(r.g(k1l >> 4), r.g(k1h >> 4));
-    Bn[p] = small_to_h2(r.g(k2l >> 4), r.g(k2h >> 4));
+    An[p] = small_to_h2(rule.g(k1l >> 4), rule.g(k1h >> 4));
+    Bn[p] = small_to_h2(rule.g(k2l >> 4), rule.g(k2h >> 4));
     In[p] = small_to_h2(k1l & 15, k1h & 15);
     if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
   }
 
+  uint32_t SN[P];
 #pragma unroll
-  for (int j = 0; j < DMAX; ++j) {
-    if (j < d) {
-      const int n = colj<SIDX>(c, sidx, j, m);
+  for (int p = 0; p < P; ++p) SN[p] = Sn[p];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      int n;
+      if constexpr (KEEP) n = col[j];
+      else n = colj<SIDX>(c, sidx, j, m);
       uint32_t sv = 0;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const uint32_t msk = heq_mask(In[p], h2c(j));
-        const uint32_t mag = (Bn[p] & msk) | (An[p] & ~msk);
-        const uint32_t L = mag ^ ((Sn[p] << (15 - j)) & 0x80008000u);
-        atomicAdd(Acc + (size_t)n * P + p, (int32_t)hadd(L, h2c(1536)));
+        const uint32_t L = ((Bn[p] & msk) | (An[p] & ~msk)) ^ (SN[p] & 0x80008000u);
+        SN[p] += SN[p];
+        atomicAdd(Acc + n * P + p, (int32_t)hadd(L, h2c(1536)));
         if constexpr (FORM == 0) {
           const uint32_t hb = hfma(L, 0x30003000u /* 0.125 */, h2c(144));
           sv |= (uint32_t)__byte_perm(hb, 0u, 0x4420) << (16 * p);
         }
       }
       if constexpr (FORM == 0) {
-        if constexpr (P == 1) Lm[(size_t)j * M + m] = (uint16_t)sv;
-        else reinterpret_cast<uint32_t*>(Lm)[(size_t)j * M + m] = sv;
+        if constexpr (P == 1) Lm[j * M + m] = (uint16_t)sv;
+        else reinterpret_cast<uint32_t*>(Lm)[j * M + m] = sv;
       }
     }
   }
   if constexpr (FORM == 1) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) St[(size_t)m * P + p] = make_uint4(An[p], Bn[p], In[p], Sn[p]);
+    for (int p = 0; p < P; ++p) St[m * P + p] = make_uint4(An[p], Bn[p], In[p], Sn[p]);
   }
   return par;
+}
+
+// Degrees with a fully unrolled body; other degrees take the guarded loop.
+template <int DMAX>
+struct Fast {
+  static constexpr int a = DMAX <= 8 ? 6 : 14;
+  static constexpr int b = DMAX <= 8 ? 7 : 15;
+};
+
+template <int G, int FORM, int DMAX, bool ES, bool SIDX>
+__device__ __forceinline__ uint32_t check_update_h2(const DevCode& c, const H2Rule& r, uint32_t qm2, int m,
+                                                    const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
+                                                    uint4* __restrict__ St, uint16_t* __restrict__ Lm,
+                                                    const uint16_t* __restrict__ sidx) {
+  const int d = c.deg(m);
+  if (d == Fast<DMAX>::a)
+    return check_body<G, FORM, Fast<DMAX>::a, DMAX, ES, SIDX>(c, r, qm2, m, d, Zs, Acc, St, Lm, sidx);
+  if (d == Fast<DMAX>::b)
+    return check_body<G, FORM, Fast<DMAX>::b, DMAX, ES, SIDX>(c, r, qm2, m, d, Zs, Acc, St, Lm, sidx);
+  return check_body<G, FORM, 0, DMAX, ES, SIDX>(c, r, qm2, m, d, Zs, Acc, St, Lm, sidx);
+}
+
+template <int G, int DMAX, bool SIDX>
+__device__ __forceinline__ uint32_t row_parity_h2(const DevCode& c, const uint16_t* __restrict__ sidx,
+                                                  const uint32_t* __restrict__ Zs, int m) {
+  return row_parity_body<G, 0, DMAX, SIDX>(c, sidx, Zs, m, c.deg(m));
 }
 
 __device__ __forceinline__ int32_t q0v(const int8_t* __restrict__ llr, int32_t N, int32_t f, int32_t F, int n) {
@@ -231,6 +290,7 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
   const int tid = threadIdx.x, nt = blockDim.x;
   const int N8 = (N + 7) >> 3;
   const uint32_t qm2 = ints_to_h2(r.qm, r.qm);
+  const H2Rule hr = make_h2rule(r);
   if constexpr (SIDX) {
     // the column table is the same for every frame group: copy it once
     const int words = (c.ell_w * M) >> 1;
@@ -272,7 +332,7 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
       const int kp = k & 1;
       uint32_t fail = 0;
       for (int m = tid; m < M; m += nt)
-        fail |= check_update_h2<G, FORM, DMAX, ES, SIDX>(c, r, qm2, m, Zs, Acc, St, Lm, sidx);
+        fail |= check_update_h2<G, FORM, DMAX, ES, SIDX>(c, hr, qm2, m, Zs, Acc, St, Lm, sidx);
       if constexpr (ES) {
         fail = __reduce_or_sync(0xffffffffu, fail);
         if ((tid & 31) == 0 && (fail & act)) atomicOr(&s_fail[kp], fail & act);
@@ -373,7 +433,9 @@ cudaError_t h2_dispatch_es(bool es, const DevCode& c, const IntRule& r, OnchipPl
 
 }  // namespace
 
-bool onchip_h2_eligible(int n_vars, int max_row_deg, int max_col_deg, int qm) {
+bool onchip_h2_eligible(int n_vars, int max_row_deg, int max_col_deg, int qm, int rule, int num) {
+  (void)rule;
+  (void)num;
   return n_vars <= 65535 && max_row_deg <= 16 && 128 + (int64_t)max_col_deg * qm + qm <= 2048;
 }
 
@@ -385,12 +447,14 @@ bool onchip_h2_plan(const DevCode& c, int form, int32_t n_frames, int sm_count, 
   };
   // The column table in shared memory removes the L2 round trips of the index
   // loads; it is preferred over a larger frame group.
+  // Two frame pairs per thread only for checks of degree <= 8 (registers).
+  const int gmax = max_row_deg <= 8 ? 4 : 2;
   int G = 0;
   bool sidx = false;
-  for (int g : {4, 2})
+  for (int g = gmax; g >= 2; g /= 2)
     if (fits(g, true)) { G = g; sidx = true; break; }
   if (G == 0)
-    for (int g : {4, 2})
+    for (int g = gmax; g >= 2; g /= 2)
       if (fits(g, false)) { G = g; break; }
   if (G == 0) return false;
   while (G > 2 && (int64_t)n_frames < (int64_t)sm_count * G) G /= 2;
@@ -414,11 +478,9 @@ cudaError_t onchip_h2_launch(const DevCode& c, const IntRule& r, int form, Onchi
   if (plan.G == GG && form == FF && plan.dmax == DD)                                                        \
     return h2_dispatch_es<GG, FF, DD>(es, c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, \
                                       occupancy_only);
-  LDPC_H2_CASE(4, 1, 16)
   LDPC_H2_CASE(2, 1, 16)
   LDPC_H2_CASE(4, 1, 8)
   LDPC_H2_CASE(2, 1, 8)
-  LDPC_H2_CASE(4, 0, 16)
   LDPC_H2_CASE(2, 0, 16)
   LDPC_H2_CASE(4, 0, 8)
   LDPC_H2_CASE(2, 0, 8)
