@@ -11,6 +11,9 @@ inside the timed region.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload qc_n7493]
                   [--form ss_1bit|ss_fixed] [--impl ours|reference]
 
+``--workload multi8`` times the uneven eight-code batch (ldpc_multi_* plan,
+autotuned, one CUDA graph replay per step).
+
 ``--impl reference`` times the CPU oracle (the only reference this method has)
 on a bounded sample of the same workload and prints the same JSON line.
 Multi-GPU (torchrun): every rank decodes its own batch (frames are independent;
@@ -175,6 +178,28 @@ def dist_setup(args):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
+    if args.workload == "multi8":
+        ws = I.make_multi_workload()
+        for w in ws:
+            w.params["early_stop"] = 0
+        budget = float(os.environ.get("BENCH_REF_BUDGET_S", "4"))
+        vals = []
+        for s in range(args.warmup + args.steps):
+            info = cpu_oracle_multi_sample(ws, args.form, budget if s >= args.warmup else 1.0)
+            if s >= args.warmup:
+                vals.append(info["value"])
+        val = float(np.median(vals))
+        info["value"] = val
+        bits = sum(w.n_frames * w.K for w in ws)
+        line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": bits / (val * 1e9) * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+                "config": {"workload": "multi8", "form": args.form, "codes": [w.name for w in ws],
+                           "n_frames": [w.n_frames for w in ws], "iters": 30},
+                "impl": "reference", "cpu_baseline": info,
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     w = I.make_workload(args.workload)
     w.params["early_stop"] = 0
     budget = float(os.environ.get("BENCH_REF_BUDGET_S", "4"))
@@ -199,6 +224,143 @@ def run_reference(args, world, rank):
     return 0
 
 
+def cpu_oracle_multi_sample(ws, form: str, budget_s: float):
+    """Times the CPU oracle on frames of every code of the batch in turn (the
+    same frames per code share) until ``budget_s`` seconds."""
+    import oracle
+    chunk = max(oracle.default_threads(), 4)
+    t_total, bits_done, frames_done = 0.0, 0, 0
+    rnd = 0
+    while t_total < budget_s:
+        for w in ws:
+            p = w.params
+            q = w.q0[(rnd * chunk) % w.n_frames:][:chunk]
+            t0 = time.perf_counter()
+            oracle.decode_int(w.code, q, form=form, rule=p["rule"], offset=p.get("offset", 0),
+                              norm_num=p.get("norm_num", 3), norm_shift=p.get("norm_shift", 2),
+                              msg_sat=p["msg_sat"], max_iter=p["max_iter"], early_stop=0)
+            t_total += time.perf_counter() - t0
+            bits_done += q.shape[0] * w.K
+            frames_done += q.shape[0]
+        rnd += 1
+    return dict(value=bits_done / t_total / 1e9, unit=UNIT, cores=oracle.default_threads(), kind="oracle",
+                sample=f"{frames_done} frames, {chunk} per code per round over the 8 codes of multi8, "
+                       f"30 iterations, early stop off, {form}, {t_total:.1f} s")
+
+
+def run_multi(args, world, rank, local):
+    """The uneven eight-code batch: one plan (ldpc_multi_*), autotuned, captured
+    once in a CUDA graph; a step is one graph replay decoding every frame of
+    every code."""
+    import torch
+    from paper_cs_0609090_gb300 import ldpc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ws = I.make_multi_workload(frame_seed=1 + rank)
+    for w in ws:
+        w.params["early_stop"] = 0
+    codes = [ldpc.Code.from_inputs(w.code, device=local) for w in ws]
+    llrs = [torch.from_numpy(w.q0).to(dev) for w in ws]
+    params = [ldpc.make_params(form=args.form, **w.params) for w in ws]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        mb = ldpc.MultiBatch(codes, llrs, params)
+        shape, tuned_ms = mb.autotune(reps=2, stream=stream)
+    info = mb.info()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            mb.decode(stream=stream)
+    torch.cuda.synchronize()
+    for (bits, iters, ok, _), w in zip(mb.outputs, ws):
+        assert int(iters.min()) == w.params["max_iter"] and int(iters.max()) == w.params["max_iter"]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        mb.decode(stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)
+            evs[s][0].record(stream)
+            graph.replay()
+            evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = float(np.sum([a.elapsed_time(b) for a, b in evs]))
+
+    h_llrs = [torch.from_numpy(w.q0).pin_memory() for w in ws]
+    h_out = [tuple(t.cpu().pin_memory() for t in o[:3]) for o in mb.outputs]
+    e2e_evs = []
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for d, h in zip(llrs, h_llrs):
+                d.copy_(h, non_blocking=True)
+            mb.decode(stream=stream)
+            for o, h in zip(mb.outputs, h_out):
+                for dt, ht in zip(o[:3], h):
+                    ht.copy_(dt, non_blocking=True)
+            b.record(stream)
+            e2e_evs.append((a, b))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    e2e_ms = float(np.sum([a.elapsed_time(b) for a, b in e2e_evs]))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+        dist.barrier()
+    if rank != 0:
+        return 0
+    ms_step = total_ms / args.steps
+    info_bits = sum(w.n_frames * w.K for w in ws)
+    value = world * info_bits / (ms_step * 1e-3) / 1e9
+    e2e_val = world * info_bits / (e2e_ms / args.steps * 1e-3) / 1e9
+    ab = sum(algorithmic_bytes(w.code, args.form, w.params["max_iter"], w.n_frames)["per_launch"] for w in ws)
+    peaks = measured_peaks()
+    achieved = ab / (ms_step * 1e-3) / 1e9
+    n_stream = sum(1 for v in info["job_is_cluster"] if v == 2)
+    launches = (1 if n_stream < len(ws) else 0) + n_stream * (3 + 2 * 30)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": "multi8", "form": args.form, "codes": [w.name for w in ws],
+                       "n_frames": [w.n_frames for w in ws], "iters": 30, "early_stop": 0,
+                       "ebn0_db": [w.ebn0_db for w in ws], "graph": "one CUDA graph replay per step",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "plan": {k: info[k] for k in ("threads", "team_threads", "cluster", "queue", "large",
+                                                    "grid", "smem_bytes", "job_is_cluster",
+                                                    "job_pairs_per_cta")},
+                       "autotune_ms": tuned_ms},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(sum(w.q0.nbytes for w in ws)),
+                    "d2h_bytes_per_step": int(sum(sum(t.numel() * t.element_size() for t in o[:3])
+                                                  for o in mb.outputs))},
+            "gpu_launches": args.steps * launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": peaks["source"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_launch": ab,
+                         "kernel": "graph (multi_h2_kernel + streaming kernels of the codes that do not fit a CTA)",
+                         "kernel_ms": ms_step},
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_multi_sample(ws, args.form,
+                                                       float(os.environ.get("BENCH_CPU_BUDGET_S", "12")))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,7 +369,7 @@ def main():
     ap.add_argument("--workload", default="qc_n7493")
     ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half", "stream"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half", "stream", "cluster"])
     ap.add_argument("--dtype", default="int8", choices=["int8", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -215,6 +377,9 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+
+    if args.workload == "multi8":
+        return run_multi(args, world, rank, local)
 
     import torch
     from paper_cs_0609090_gb300 import ldpc

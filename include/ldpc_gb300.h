@@ -88,6 +88,12 @@ enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2 };
  *                LDPC_KERNEL_STREAM       frame state in device memory (the
  *                                         workspace); for codes too large for one
  *                                         SM; the only kernel of the float32 path
+ *                LDPC_KERNEL_CLUSTER      a frame pair spread over the CTAs of a
+ *                                         thread-block cluster (distributed shared
+ *                                         memory), the packed binary16 arithmetic
+ *                                         of ONCHIP_HALF with its conditions; for
+ *                                         int8 single-scan codes too large for
+ *                                         one SM; no workspace
  */
 typedef struct {
   int32_t dtype;
@@ -104,7 +110,13 @@ typedef struct {
   int32_t kernel;
 } ldpc_decode_params;
 
-enum { LDPC_KERNEL_AUTO = 0, LDPC_KERNEL_ONCHIP_INT = 1, LDPC_KERNEL_ONCHIP_HALF = 2, LDPC_KERNEL_STREAM = 3 };
+enum {
+  LDPC_KERNEL_AUTO = 0,
+  LDPC_KERNEL_ONCHIP_INT = 1,
+  LDPC_KERNEL_ONCHIP_HALF = 2,
+  LDPC_KERNEL_STREAM = 3,
+  LDPC_KERNEL_CLUSTER = 4
+};
 
 /* Build a code from the check->variable adjacency N(m) of H (Section II).
  *   row_ptr  host, [n_checks + 1], row_ptr[0] = 0, non-decreasing.
@@ -261,6 +273,94 @@ LDPC_API ldpc_status ldpc_decode_batch_noalloc(const ldpc_code *code, const ldpc
                                                const void *llr, int32_t n_frames, uint8_t *hard_bits,
                                                int32_t *iters_used, uint8_t *syndrome_ok, void *llr_out,
                                                void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batches over several codes.  (A throughput interface of this library; the
+ * paper decodes one code at a time.)  Every job is an int8 single-scan decode
+ * with outputs identical to ldpc_decode_batch's.  The codes whose frame pair
+ * fits one CTA share one persistent kernel launch in which frame pairs are
+ * handed out longest first from a work queue, several pairs per CTA on
+ * sub-teams of its threads.  A larger code either runs the streaming decoder
+ * (frame state in the workspace) after that launch on the same stream, or is
+ * decoded inside the same persistent launch by all CTAs of a thread-block
+ * cluster (tuning.large).
+ * ------------------------------------------------------------------------ */
+
+/* One code of a batch.
+ *   code        a code created on the batch's device.
+ *   params      dtype LDPC_DTYPE_INT8, form SS_FIXED or SS_1BIT (the same form
+ *               for every job of a batch), any rule; kernel is ignored.  The
+ *               code must meet the binary16 conditions of LDPC_KERNEL_ONCHIP_HALF.
+ *   llr, n_frames and the outputs: device buffers as in ldpc_decode_batch
+ *   (llr_out may be NULL).  n_frames == 0 drops the job. */
+typedef struct {
+  const ldpc_code *code;
+  ldpc_decode_params params;
+  const int8_t *llr;
+  int32_t n_frames;
+  uint8_t *hard_bits;
+  int32_t *iters_used;
+  uint8_t *syndrome_ok;
+  int16_t *llr_out;
+} ldpc_multi_job;
+
+/* Launch shape of a batch (0 in a field means the default).
+ *   threads       threads per CTA: 256, 512, 768 or 1024 (default 1024).
+ *   team_threads  fewest threads that decode one frame pair of a code that fits
+ *                 one CTA; a CTA holds threads / team_threads such pairs when
+ *                 shared memory allows (32..1024, power of two; default 128).
+ *   cluster       CTAs per cluster for codes that do not fit one SM: 2, 4, 8 or
+ *                 16; default the smallest that fits every such code.
+ *   queue         1 (default): dynamic work queue; 2: round-robin assignment.
+ *   large         codes whose frame pair does not fit one CTA: 1 (default) the
+ *                 streaming decoder after the persistent launch; 2 thread-block
+ *                 clusters inside the persistent launch (the whole batch in one
+ *                 kernel launch). */
+typedef struct {
+  int32_t threads;
+  int32_t team_threads;
+  int32_t cluster;
+  int32_t queue;
+  int32_t large;
+} ldpc_multi_tuning;
+
+typedef struct ldpc_multi ldpc_multi;
+
+/* Plan a batch of n_jobs (1..16) jobs.  jobs: host array, copied; the device
+ * buffers it names are bound to the plan (every ldpc_multi_decode reads and
+ * writes those buffers).  tuning: host, nullable.  Checks every job and fails
+ * with LDPC_ERR_UNSUPPORTED (and a message naming the job) if one cannot run. */
+LDPC_API ldpc_status ldpc_multi_create(ldpc_multi **out, const ldpc_multi_job *jobs, int32_t n_jobs,
+                                       const ldpc_multi_tuning *tuning);
+LDPC_API ldpc_status ldpc_multi_destroy(ldpc_multi *plan);
+
+/* Device workspace bytes of ldpc_multi_decode: the queue counters and the
+ * frame state of the codes on the streaming decoder. */
+LDPC_API ldpc_status ldpc_multi_workspace_size(const ldpc_multi *plan, size_t *bytes);
+
+/* Decode every job of the plan on `stream`: a cudaMemsetAsync of the queue
+ * counters, the persistent kernel launch, and the streaming decoder's memsets
+ * and launches for the codes that run on it; no allocation, no host
+ * synchronisation, so the call can be captured in a CUDA graph and replayed.
+ * workspace: device, 256-byte aligned, at least ldpc_multi_workspace_size
+ * bytes, not shared with another call in flight. */
+LDPC_API ldpc_status ldpc_multi_decode(const ldpc_multi *plan, void *workspace, size_t ws_bytes, void *stream);
+
+/* Times the candidate launch shapes (threads, team_threads, large, cluster) on the
+ * plan's own buffers, reps decodes each after one warm-up, with CUDA events on
+ * `stream` (synchronising it), and keeps the fastest.  The decodes overwrite
+ * the outputs (with the same values).  Not capturable.  chosen (host,
+ * nullable) receives the kept shape, best_ms (host, nullable) its mean time. */
+LDPC_API ldpc_status ldpc_multi_autotune(ldpc_multi *plan, void *workspace, size_t ws_bytes, int32_t reps,
+                                         void *stream, ldpc_multi_tuning *chosen, float *best_ms);
+
+/* Description of the plan: the shape in use, CTAs launched, cluster size,
+ * dynamic shared memory per CTA, and per job (arrays of n_jobs entries,
+ * nullable) where it runs (0 CTA sub-teams, 1 a cluster, 2 the streaming
+ * decoder, -1 a job without frames) and the frame pairs a CTA holds at once. */
+LDPC_API ldpc_status ldpc_multi_info(const ldpc_multi *plan, ldpc_multi_tuning *shape, int32_t *grid,
+                                     int32_t *cluster, int32_t *smem_bytes, int32_t *job_is_cluster,
+                                     int32_t *job_pairs_per_cta);
 
 /* Message describing the last failed call on this thread ("" if none). */
 LDPC_API const char *ldpc_last_error(void);

@@ -1,0 +1,238 @@
+// h2_body.cuh -- one check of single-scan min-sum on packed binary16 frame pairs,
+// shared by the frame-resident kernels (onchip_h2.cu: one CTA per frame group;
+// multi_h2.cu: CTA sub-teams and thread-block clusters).
+//
+// Eq. (3) of Section IV with the Section V state (FORM 1: A, B, n~ and the signs
+// per check) or per-edge messages (FORM 0).  Every quantity is an integer of
+// magnitude < 2048, so binary16 holds it exactly and every f16x2 add, fma, min and
+// max below is exact: the results are bit-identical to integer arithmetic.
+//
+// Where the posterior of a variable lives is a policy (Addr):
+//   Addr::H                    handle of variable j of check m (index or pointer)
+//   at(tab, Zs, j, m) -> H     look the handle up in the column table
+//   load(Zs, h, w[P])          posterior pairs Z^(k-1) of the variable
+//   add(Acc, h, p, v)          atomically add the message pattern v of pair p
+//   st(m), lm(j, m)            element index of check m's state / of the
+//                              message slot of its position j (pair 0)
+#pragma once
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "h2ops.cuh"
+
+namespace ldpc {
+
+template <int G>
+__device__ __forceinline__ void ld_pairs(const uint32_t* __restrict__ Zs, int n, uint32_t (&w)[G / 2]) {
+  if constexpr (G == 2) {
+    w[0] = Zs[n];
+  } else {
+    const uint2 v = reinterpret_cast<const uint2*>(Zs)[n];
+    w[0] = v.x;
+    w[1] = v.y;
+  }
+}
+template <int G>
+__device__ __forceinline__ void st_pairs(uint32_t* __restrict__ Zs, int n, const uint32_t (&w)[G / 2]) {
+  if constexpr (G == 2) Zs[n] = w[0];
+  else reinterpret_cast<uint2*>(Zs)[n] = make_uint2(w[0], w[1]);
+}
+
+// The policies hold only scalars: the table and posterior pointers are passed to
+// check_body as __restrict__ parameters, so that loads of the table and of Zs
+// may move past the accumulator atomics.
+//
+// Posteriors of this CTA's shared memory: Zs [N][P] half2, Acc [N][P] i32, with
+// the edge-slot-major column table in shared memory (SIDX) or global memory.
+template <int G, bool SIDX>
+struct LocalAddr {
+  static constexpr int P = G / 2;
+  using H = int;
+  int M;
+  __device__ __forceinline__ H at(const uint16_t* __restrict__ tab, const uint32_t*, int j, int m) const {
+    if constexpr (SIDX) return (int)tab[j * M + m];
+    else return (int)__ldg(tab + j * M + m);
+  }
+  __device__ __forceinline__ void load(const uint32_t* __restrict__ Zs, H n, uint32_t (&w)[P]) const {
+    ld_pairs<G>(Zs, n, w);
+  }
+  __device__ __forceinline__ void add(int32_t* __restrict__ Acc, H n, int p, int32_t v) const {
+    atomicAdd(Acc + n * P + p, v);
+  }
+  __device__ __forceinline__ int st(int m) const { return m * P; }
+  __device__ __forceinline__ int lm(int j, int m) const { return j * M + m; }
+};
+
+// |x| of both halves (an operand modifier of the instruction that consumes it).
+__device__ __forceinline__ uint32_t hab(uint32_t a) {
+  uint32_t d; asm("abs.f16x2 %0, %1;" : "=r"(d) : "r"(a)); return d;
+}
+
+// Section III's magnitude rule without branches: g(x) = max((x - beta) num, 0)
+// >> shift (plain: beta 0, num 1, shift 0; offset: beta, 1, 0; normalized: 0,
+// num, shift), which floors the normalized magnitude like the integer rule.
+struct H2Rule {
+  int32_t beta, num, shift;
+  __device__ __forceinline__ int32_t g(int32_t x) const { return max((x - beta) * num, 0) >> shift; }
+};
+__host__ __device__ inline H2Rule make_h2rule(const IntRule& r) {
+  H2Rule h;
+  h.beta = r.rule == 1 ? r.beta : 0;
+  h.num = r.rule == 2 ? r.num : 1;
+  h.shift = r.rule == 2 ? r.shift : 0;
+  return h;
+}
+
+// Decision parity of check m for the G frames (bit g set: unsatisfied).
+template <int G, int D, int DMAX, class Addr>
+__device__ __forceinline__ uint32_t row_parity_body(const Addr& ad, const uint16_t* __restrict__ tab,
+                                                    const uint32_t* __restrict__ Zs, int m, int d) {
+  constexpr int P = G / 2;
+  constexpr int NJ = D > 0 ? D : DMAX;
+  uint32_t y[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) y[p] = 0;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      uint32_t w[P];
+      ad.load(Zs, ad.at(tab, Zs, j, m), w);
+#pragma unroll
+      for (int p = 0; p < P; ++p) y[p] ^= dec_bits(w[p]);
+    }
+  }
+  uint32_t par = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) par |= ((y[p] >> 15) & 1u) << (2 * p) | ((y[p] >> 31) & 1u) << (2 * p + 1);
+  return par;
+}
+
+// One check m for all G frames: Eq. (3) with the Section V state (FORM 1) or
+// per-edge messages (FORM 0).  D > 0: the check has exactly D positions (fully
+// unrolled); D == 0: d <= DMAX positions, guarded.  Returns the decision parity
+// bits of x^(k-1) when ES.
+//   St  (FORM 1) [rows][P] {A, B, n~ as half2; signs, bit-reversed: the sign of
+//       position j of the even frame at bit 15 - j, of the odd frame at bit
+//       31 - j, so that shifting the word left by j (a running S + S) brings both
+//       to the binary16 sign bits}
+//   Lm  (FORM 0) [ell_w][rows][P] u16: L + 128 per frame (one byte each)
+template <int G, int FORM, int D, int DMAX, bool ES, class Addr>
+__device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* __restrict__ tab,
+                                               const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
+                                               const H2Rule& rule, uint32_t qm2, int m, int d,
+                                               uint4* __restrict__ St, uint16_t* __restrict__ Lm) {
+  constexpr int P = G / 2;
+  constexpr int NJ = D > 0 ? D : DMAX;
+  // one frame pair: the pass-1 handles stay in registers for pass 2; two pairs
+  // need those registers for state and reload them
+  constexpr bool KEEP = (P == 1 && FORM == 1 && !ES);
+  using H = typename Addr::H;
+  uint32_t A2[P], B2[P], I2[P], S[P];
+  if constexpr (FORM == 1) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const uint4 s = St[ad.st(m) + p];
+      A2[p] = s.x;
+      B2[p] = s.y;
+      I2[p] = s.z;
+      S[p] = s.w;
+    }
+  }
+  uint32_t K1[P], K2[P], NEG[P], Y[P], SR[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    K1[p] = h2c(2048);
+    K2[p] = h2c(2048);
+    NEG[p] = 0;
+    Y[p] = 0;
+    if constexpr (FORM == 1) SR[p] = S[p];
+  }
+  H col[KEEP ? NJ : 1];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      const H n = ad.at(tab, Zs, j, m);
+      if constexpr (KEEP) col[j] = n;
+      uint32_t w[P];
+      ad.load(Zs, n, w);
+      uint32_t lv = 0;
+      if constexpr (FORM == 0) {
+        if constexpr (P == 1) lv = Lm[ad.lm(j, m)];
+        else lv = reinterpret_cast<const uint32_t*>(Lm)[ad.lm(j, m)];
+      }
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        uint32_t L;
+        if constexpr (FORM == 1) {
+          // f(A, B, n, n~) and the stored sign s_mn on the binary16 sign bit
+          const uint32_t msk = heq_mask(I2[p], h2c(j));
+          L = ((B2[p] & msk) | (A2[p] & ~msk)) ^ (SR[p] & 0x80008000u);
+          SR[p] += SR[p];
+        } else {
+          // byte L + 128 -> binary16 128 + (L + 128)/8 -> 8 h - 1152 = L
+          const uint32_t b = (P == 1) ? lv : (lv >> (16 * p));
+          L = hfma(__byte_perm(b, 0x58u, 0x4140), h2c(8), 0xE480E480u /* -1152 */);
+        }
+        const uint32_t u = hsub(w[p], L);
+        if constexpr (ES) Y[p] ^= dec_bits(w[p]);
+        NEG[p] |= (u >> j) & (0x80008000u >> j);  // sign of u_j at bit 15 - j / 31 - j
+        const uint32_t key = hfma(hmin(hab(u), qm2), h2c(16), h2c(j));
+        K2[p] = hmin(K2[p], hmax(K1[p], key));
+        K1[p] = hmin(K1[p], key);
+      }
+    }
+  }
+
+  const int dd = D > 0 ? D : d;
+  const uint32_t dlane = ((1u << dd) - 1u) << (16 - dd);  // bits 16-d .. 15
+  uint32_t An[P], Bn[P], In[P], Sn[P];
+  uint32_t par = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    // sign of L^(k)_mj = parity of all input signs xor own sign
+    const uint32_t pm = ((__popc(NEG[p] & 0xffffu) & 1) ? 0x0000ffffu : 0u) |
+                        ((__popc(NEG[p] >> 16) & 1) ? 0xffff0000u : 0u);
+    Sn[p] = (NEG[p] ^ pm) & (dlane | (dlane << 16));
+    const int32_t k1l = h_lo_int(K1[p]), k1h = h_hi_int(K1[p]);
+    const int32_t k2l = h_lo_int(K2[p]), k2h = h_hi_int(K2[p]);
+    An[p] = small_to_h2(rule.g(k1l >> 4), rule.g(k1h >> 4));
+    Bn[p] = small_to_h2(rule.g(k2l >> 4), rule.g(k2h >> 4));
+    In[p] = small_to_h2(k1l & 15, k1h & 15);
+    if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
+  }
+
+  uint32_t SN[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) SN[p] = Sn[p];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      H n;
+      if constexpr (KEEP) n = col[j];
+      else n = ad.at(tab, Zs, j, m);
+      uint32_t sv = 0;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const uint32_t msk = heq_mask(In[p], h2c(j));
+        const uint32_t L = ((Bn[p] & msk) | (An[p] & ~msk)) ^ (SN[p] & 0x80008000u);
+        SN[p] += SN[p];
+        ad.add(Acc, n, p, (int32_t)hadd(L, h2c(1536)));
+        if constexpr (FORM == 0) {
+          const uint32_t hb = hfma(L, 0x30003000u /* 0.125 */, h2c(144));
+          sv |= (uint32_t)__byte_perm(hb, 0u, 0x4420) << (16 * p);
+        }
+      }
+      if constexpr (FORM == 0) {
+        if constexpr (P == 1) Lm[ad.lm(j, m)] = (uint16_t)sv;
+        else reinterpret_cast<uint32_t*>(Lm)[ad.lm(j, m)] = sv;
+      }
+    }
+  }
+  if constexpr (FORM == 1) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) St[ad.st(m) + p] = make_uint4(An[p], Bn[p], In[p], Sn[p]);
+  }
+  return par;
+}
+
+}  // namespace ldpc

@@ -50,12 +50,49 @@ cudaError_t onchip_twoscan_launch(const DevCode& c, const IntRule& r, OnchipPlan
                                   const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
                                   int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t stream);
 
+// Persistent multi-code launch (multi_h2.cu).  Jobs [0, n_cjobs) are cluster
+// jobs (one frame pair per cluster of cs CTAs), the rest local jobs (`sub` frame
+// pairs per CTA, one per sub-team); items are numbered per queue from item0.
+constexpr int kMultiMaxJobs = 16;
+constexpr int kMultiMaxSub = 8;
+struct MultiJob {
+  int32_t N, M, ell_w;
+  int32_t mr;       // rows per table (local: M; cluster: row capacity of a rank, even)
+  int32_t ns, lb;   // cluster: variables per rank, local-index bits of a table entry
+  int32_t sub;      // local: frame pairs per CTA
+  int32_t n_pairs, item0;
+  const uint16_t* tab;   // local: the code's ell16 [ell_w][M]; cluster: [cs][ell_w][mr] packed
+  const uint8_t* rdeg;   // local: [M]; cluster: [cs][mr]
+  const int32_t* rows;   // cluster: [cs] checks per rank
+  const int32_t* cdeg;   // [N]
+  int32_t beta, num, shift, qm, max_iter, early_stop;  // H2Rule fields, Qm, cap
+  const int8_t* llr;
+  int32_t F;
+  uint8_t* bits;
+  int32_t* iters;
+  uint8_t* ok;
+  int16_t* zout;
+  uint32_t tab_bytes, slot_bytes, acc_off, st_off;  // shared-memory layout
+};
+struct MultiParams {
+  int32_t n_jobs, n_cjobs, n_citems, n_litems, cs;
+  int32_t* counters;  // [2] zero before the launch, or nullptr: round-robin items
+  MultiJob job[kMultiMaxJobs];
+};
+// Bytes of one local pair slot (Zs, Acc, St or Lm) and its offsets.
+size_t multi_local_slot_bytes(int N, int M, int ell_w, int form, size_t* acc_off, size_t* st_off);
+// Launches (max_grid == nullptr) or reports the persistent grid of a shape.
+cudaError_t multi_launch(int form, bool es, const MultiParams& mp, int threads, size_t smem, int grid,
+                         cudaStream_t st, int* max_grid);
+
 // Device-memory (streaming) decoders for codes whose frame state does not fit
 // one SM.  All state lives in the caller's workspace (layout below).
 struct StreamLayout {
   int lanes = 0;  // frame pairs (int8) or frames (float32), padded to 32
   size_t z = 0, acc = 0, st = 0, q0 = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
 };
+// E: message slots of the per-edge form (int8: ell_w * M edge slots of the
+// degree-sorted table; float32: the E edges of H).
 StreamLayout stream_layout(int dtype, int form, int N, int M, int E, int F);
 bool stream_int8_eligible(int max_row_deg, int max_col_deg, int qm);
 cudaError_t stream_int8_decode(const DevCode& c, const IntRule& r, int form, const StreamLayout& L, void* ws,

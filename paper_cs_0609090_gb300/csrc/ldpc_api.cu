@@ -8,34 +8,17 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ldpc_gb300.h"
-#include "kernels.h"
+#include "api_internal.h"
 
-struct ldpc_code {
-  int device = 0;
-  int32_t N = 0, M = 0, E = 0;
-  int32_t max_row_deg = 0, max_col_deg = 0;
-  int32_t* d_rp = nullptr;
-  int32_t* d_ci = nullptr;
-  int32_t* d_cdeg = nullptr;
-  uint16_t* d_ell16 = nullptr;
-  int32_t* d_ell32 = nullptr;
-  uint8_t* d_rdeg = nullptr;
-  int32_t* d_cptr = nullptr;
-  int32_t* d_cslot = nullptr;
-  uint8_t* d_rclass = nullptr;      // degree class of every check
-  int32_t n_classes = 0;
-  int32_t class_deg[32] = {};       // check degree of each class, ascending
-  int32_t ell_w = 0;
-  int sm_count = 0;
-  size_t smem_optin = 0;
-};
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
-ldpc_status fail(ldpc_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+namespace ldpc_api {
+
+void clear_error() { g_last_error.clear(); }
+
 ldpc_status fail(ldpc_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -51,20 +34,6 @@ ldpc_status cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? LDPC_ERR_OOM : LDPC_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 ldpc::DevCode view(const ldpc_code* c) {
   ldpc::DevCode v;
@@ -93,7 +62,7 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   if (p->max_iter < 0) return fail(LDPC_ERR_INVALID_ARG, "max_iter %d < 0", p->max_iter);
   if (p->early_stop != 0 && p->early_stop != 1)
     return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");
-  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_STREAM)
+  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_CLUSTER)
     return fail(LDPC_ERR_INVALID_ARG, "kernel %d is not a known LDPC_KERNEL_*", p->kernel);
   if (p->dtype == LDPC_DTYPE_INT8) {
     if (p->msg_sat < 1 || p->msg_sat > 127)
@@ -118,9 +87,15 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   return LDPC_OK;
 }
 
+}  // namespace ldpc_api
+
+using namespace ldpc_api;
+
+namespace {
+
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
-  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, STREAM_INT8, STREAM_F32, ONCHIP_TWOSCAN } kind = NONE;
+  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, STREAM_F32, ONCHIP_TWOSCAN } kind = NONE;
   ldpc::OnchipPlan onchip;
   ldpc::StreamLayout stream;
   size_t ws = 0;
@@ -133,9 +108,15 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     const bool want_half = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF;
     const bool want_int = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_INT;
     const bool want_stream = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM;
+    const bool want_cluster = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_CLUSTER;
     if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num) &&
         ldpc::onchip_h2_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_H2;
+      ch->ws = 0;
+      return LDPC_OK;
+    }
+    if (want_cluster && cluster_plan_fits(c, p)) {
+      ch->kind = Choice::CLUSTER_H2;
       ch->ws = 0;
       return LDPC_OK;
     }
@@ -146,7 +127,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     }
     if (want_stream && ldpc::stream_int8_eligible(c->max_row_deg, c->max_col_deg, p->msg_sat)) {
       ch->kind = Choice::STREAM_INT8;
-      ch->stream = ldpc::stream_layout(0, form, c->N, c->M, c->E, n_frames);
+      ch->stream = ldpc::stream_layout(0, form, c->N, c->M, c->ell_w * c->M, n_frames);
       ch->ws = ch->stream.total;
       return LDPC_OK;
     }
@@ -317,6 +298,11 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
     delete c;
     return cuda_fail(err, "ldpc_code_create device copy");
   }
+  const ldpc_status cs = build_cluster_tables(c, row_ptr, col_idx);
+  if (cs != LDPC_OK) {
+    ldpc_code_destroy(c);
+    return cs;
+  }
   *out = c;
   return LDPC_OK;
 }
@@ -335,6 +321,7 @@ ldpc_status ldpc_code_destroy(ldpc_code* code) {
   cudaFree(code->d_cptr);
   cudaFree(code->d_cslot);
   cudaFree(code->d_rclass);
+  free_cluster_tables(code);
   delete code;
   return LDPC_OK;
 }
@@ -407,6 +394,9 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
     err = ldpc::onchip_h2_launch(v, r, form, ch.onchip, code->sm_count, static_cast<const int8_t*>(llr), n_frames,
                                  params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
                                  static_cast<int16_t*>(llr_out), st, false);
+  } else if (ch.kind == Choice::CLUSTER_H2) {
+    err = cluster_decode(code, params, static_cast<const int8_t*>(llr), n_frames, hard_bits, iters_used, syndrome_ok,
+                         static_cast<int16_t*>(llr_out), st);
   } else if (ch.kind == Choice::STREAM_INT8) {
     err = ldpc::stream_int8_decode(v, r, form, ch.stream, workspace, code->sm_count, static_cast<const int8_t*>(llr),
                                    n_frames, params->max_iter, params->early_stop, hard_bits, iters_used,
@@ -593,7 +583,7 @@ ldpc_status ldpc_decode_batch_noalloc(const ldpc_code* code, const ldpc_decode_p
   if (llr == nullptr || hard_bits == nullptr || iters_used == nullptr || syndrome_ok == nullptr)
     return fail(LDPC_ERR_INVALID_ARG, "llr, hard_bits, iters_used and syndrome_ok must be non-NULL");
   const int form = params->form == LDPC_FORM_SS_1BIT ? 1 : 0;
-  const ldpc::StreamLayout L = ldpc::stream_layout(0, form, code->N, code->M, code->E, n_frames);
+  const ldpc::StreamLayout L = ldpc::stream_layout(0, form, code->N, code->M, code->ell_w * code->M, n_frames);
   if (L.total > (size_t)LDPC_NOALLOC_SCRATCH_BYTES)
     return fail(LDPC_ERR_UNSUPPORTED,
                 "%d frames of this code need %zu bytes of scratch; the static scratch holds %zu "

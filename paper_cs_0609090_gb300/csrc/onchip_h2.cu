@@ -23,7 +23,7 @@
 //   form 0 (Section IV): [E][P] u16: L + 128 per frame (one byte each)
 #include <cuda_fp16.h>
 
-#include "h2ops.cuh"
+#include "h2_body.cuh"
 #include "kernels.h"
 
 namespace ldpc {
@@ -49,197 +49,6 @@ __host__ __device__ inline H2Layout h2_layout(int N, int M, int E, int G, int fo
   return L;
 }
 
-template <int G>
-__device__ __forceinline__ void ld_pairs(const uint32_t* __restrict__ Zs, int n, uint32_t (&w)[G / 2]) {
-  if constexpr (G == 2) {
-    w[0] = Zs[n];
-  } else {
-    const uint2 v = reinterpret_cast<const uint2*>(Zs)[n];
-    w[0] = v.x;
-    w[1] = v.y;
-  }
-}
-template <int G>
-__device__ __forceinline__ void st_pairs(uint32_t* __restrict__ Zs, int n, const uint32_t (&w)[G / 2]) {
-  if constexpr (G == 2) Zs[n] = w[0];
-  else reinterpret_cast<uint2*>(Zs)[n] = make_uint2(w[0], w[1]);
-}
-
-// Column of position j of check m: from the shared-memory copy or from global.
-// Column of position j of internal check m: shared-memory copy or global table.
-template <bool SIDX>
-__device__ __forceinline__ int colj(const DevCode& c, const uint16_t* __restrict__ sidx, int j, int m) {
-  if constexpr (SIDX) return (int)sidx[j * c.M + m];
-  else return (int)__ldg(c.ell16 + j * c.M + m);
-}
-
-// |x| of both halves (an operand modifier of the instruction that consumes it).
-__device__ __forceinline__ uint32_t hab(uint32_t a) {
-  uint32_t d; asm("abs.f16x2 %0, %1;" : "=r"(d) : "r"(a)); return d;
-}
-
-// Decision parity of check m for the G frames (bit g set: unsatisfied).
-template <int G, int D, int DMAX, bool SIDX>
-__device__ __forceinline__ uint32_t row_parity_body(const DevCode& c, const uint16_t* __restrict__ sidx,
-                                                    const uint32_t* __restrict__ Zs, int m, int d) {
-  constexpr int P = G / 2;
-  constexpr int NJ = D > 0 ? D : DMAX;
-  uint32_t y[P];
-#pragma unroll
-  for (int p = 0; p < P; ++p) y[p] = 0;
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    if (D > 0 || j < d) {
-      uint32_t w[P];
-      ld_pairs<G>(Zs, colj<SIDX>(c, sidx, j, m), w);
-#pragma unroll
-      for (int p = 0; p < P; ++p) y[p] ^= dec_bits(w[p]);
-    }
-  }
-  uint32_t par = 0;
-#pragma unroll
-  for (int p = 0; p < P; ++p) par |= ((y[p] >> 15) & 1u) << (2 * p) | ((y[p] >> 31) & 1u) << (2 * p + 1);
-  return par;
-}
-
-// Section III's magnitude rule without branches: g(x) = max((x - beta) num, 0)
-// >> shift (plain: beta 0, num 1, shift 0; offset: beta, 1, 0; normalized: 0,
-// num, shift), which floors the normalized magnitude like the integer rule.
-struct H2Rule {
-  int32_t beta, num, shift;
-  __device__ __forceinline__ int32_t g(int32_t x) const { return max((x - beta) * num, 0) >> shift; }
-};
-__device__ inline H2Rule make_h2rule(const IntRule& r) {
-  H2Rule h;
-  h.beta = r.rule == 1 ? r.beta : 0;
-  h.num = r.rule == 2 ? r.num : 1;
-  h.shift = r.rule == 2 ? r.shift : 0;
-  return h;
-}
-
-// One check m for all G frames: Eq. (3) with the Section V state (FORM 1) or
-// per-edge messages (FORM 0).  D > 0: the check has exactly D positions (fully
-// unrolled); D == 0: d <= DMAX positions, guarded.  Returns the decision parity
-// bits of x^(k-1) when ES.
-template <int G, int FORM, int D, int DMAX, bool ES, bool SIDX>
-__device__ __forceinline__ uint32_t check_body(const DevCode& c, const H2Rule& rule, uint32_t qm2, int m, int d,
-                                               const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
-                                               uint4* __restrict__ St, uint16_t* __restrict__ Lm,
-                                               const uint16_t* __restrict__ sidx) {
-  constexpr int P = G / 2;
-  constexpr int NJ = D > 0 ? D : DMAX;
-  // one frame pair: the pass-1 column indices stay in registers for pass 2;
-  // two pairs need those registers for state and reload them
-  constexpr bool KEEP = (P == 1 && FORM == 1 && !ES);
-  const int M = c.M;
-  uint32_t A2[P], B2[P], I2[P], S[P];
-  if constexpr (FORM == 1) {
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const uint4 s = St[m * P + p];
-      A2[p] = s.x;
-      B2[p] = s.y;
-      I2[p] = s.z;
-      S[p] = s.w;
-    }
-  }
-  uint32_t K1[P], K2[P], NEG[P], Y[P], SR[P];
-#pragma unroll
-  for (int p = 0; p < P; ++p) {
-    K1[p] = h2c(2048);
-    K2[p] = h2c(2048);
-    NEG[p] = 0;
-    Y[p] = 0;
-    if constexpr (FORM == 1) SR[p] = S[p];
-  }
-  int col[KEEP ? NJ : 1];
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    if (D > 0 || j < d) {
-      const int n = colj<SIDX>(c, sidx, j, m);
-      if constexpr (KEEP) col[j] = n;
-      uint32_t w[P];
-      ld_pairs<G>(Zs, n, w);
-      uint32_t lv = 0;
-      if constexpr (FORM == 0) {
-        if constexpr (P == 1) lv = Lm[j * M + m];
-        else lv = reinterpret_cast<const uint32_t*>(Lm)[j * M + m];
-      }
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        uint32_t L;
-        if constexpr (FORM == 1) {
-          // f(A, B, n, n~) and the stored sign s_mn on the binary16 sign bit
-          const uint32_t msk = heq_mask(I2[p], h2c(j));
-          L = ((B2[p] & msk) | (A2[p] & ~msk)) ^ (SR[p] & 0x80008000u);
-          SR[p] += SR[p];
-        } else {
-          // byte L + 128 -> binary16 128 + (L + 128)/8 -> 8 h - 1152 = L
-          const uint32_t b = (P == 1) ? lv : (lv >> (16 * p));
-          L = hfma(__byte_perm(b, 0x58u, 0x4140), h2c(8), 0xE480E480u /* -1152 */);
-        }
-        const uint32_t u = hsub(w[p], L);
-        if constexpr (ES) Y[p] ^= dec_bits(w[p]);
-        NEG[p] |= (u >> j) & (0x80008000u >> j);  // sign of u_j at bit 15 - j / 31 - j
-        const uint32_t key = hfma(hmin(hab(u), qm2), h2c(16), h2c(j));
-        K2[p] = hmin(K2[p], hmax(K1[p], key));
-        K1[p] = hmin(K1[p], key);
-      }
-    }
-  }
-
-  const int dd = D > 0 ? D : d;
-  const uint32_t dlane = ((1u << dd) - 1u) << (16 - dd);  // bits 16-d .. 15
-  uint32_t An[P], Bn[P], In[P], Sn[P];
-  uint32_t par = 0;
-#pragma unroll
-  for (int p = 0; p < P; ++p) {
-    // sign of L^(k)_mj = parity of all input signs xor own sign
-    const uint32_t pm = ((__popc(NEG[p] & 0xffffu) & 1) ? 0x0000ffffu : 0u) |
-                        ((__popc(NEG[p] >> 16) & 1) ? 0xffff0000u : 0u);
-    Sn[p] = (NEG[p] ^ pm) & (dlane | (dlane << 16));
-    const int32_t k1l = h_lo_int(K1[p]), k1h = h_hi_int(K1[p]);
-    const int32_t k2l = h_lo_int(K2[p]), k2h = h_hi_int(K2[p]);
-    An[p] = small_to_h2(rule.g(k1l >> 4), rule.g(k1h >> 4));
-    Bn[p] = small_to_h2(rule.g(k2l >> 4), rule.g(k2h >> 4));
-    In[p] = small_to_h2(k1l & 15, k1h & 15);
-    if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
-  }
-
-  uint32_t SN[P];
-#pragma unroll
-  for (int p = 0; p < P; ++p) SN[p] = Sn[p];
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    if (D > 0 || j < d) {
-      int n;
-      if constexpr (KEEP) n = col[j];
-      else n = colj<SIDX>(c, sidx, j, m);
-      uint32_t sv = 0;
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const uint32_t msk = heq_mask(In[p], h2c(j));
-        const uint32_t L = ((Bn[p] & msk) | (An[p] & ~msk)) ^ (SN[p] & 0x80008000u);
-        SN[p] += SN[p];
-        atomicAdd(Acc + n * P + p, (int32_t)hadd(L, h2c(1536)));
-        if constexpr (FORM == 0) {
-          const uint32_t hb = hfma(L, 0x30003000u /* 0.125 */, h2c(144));
-          sv |= (uint32_t)__byte_perm(hb, 0u, 0x4420) << (16 * p);
-        }
-      }
-      if constexpr (FORM == 0) {
-        if constexpr (P == 1) Lm[j * M + m] = (uint16_t)sv;
-        else reinterpret_cast<uint32_t*>(Lm)[j * M + m] = sv;
-      }
-    }
-  }
-  if constexpr (FORM == 1) {
-#pragma unroll
-    for (int p = 0; p < P; ++p) St[m * P + p] = make_uint4(An[p], Bn[p], In[p], Sn[p]);
-  }
-  return par;
-}
-
 // Degrees with a fully unrolled body; other degrees take the guarded loop.
 template <int DMAX>
 struct Fast {
@@ -247,23 +56,18 @@ struct Fast {
   static constexpr int b = DMAX <= 8 ? 7 : 15;
 };
 
-template <int G, int FORM, int DMAX, bool ES, bool SIDX>
-__device__ __forceinline__ uint32_t check_update_h2(const DevCode& c, const H2Rule& r, uint32_t qm2, int m,
+template <int G, int FORM, int DMAX, bool ES, class Addr>
+__device__ __forceinline__ uint32_t check_update_h2(const Addr& ad, const uint16_t* __restrict__ tab,
                                                     const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
-                                                    uint4* __restrict__ St, uint16_t* __restrict__ Lm,
-                                                    const uint16_t* __restrict__ sidx) {
-  const int d = c.deg(m);
+                                                    const uint8_t* __restrict__ rdeg, const H2Rule& r,
+                                                    uint32_t qm2, int m, uint4* __restrict__ St,
+                                                    uint16_t* __restrict__ Lm) {
+  const int d = (int)__ldg(rdeg + m);
   if (d == Fast<DMAX>::a)
-    return check_body<G, FORM, Fast<DMAX>::a, DMAX, ES, SIDX>(c, r, qm2, m, d, Zs, Acc, St, Lm, sidx);
+    return check_body<G, FORM, Fast<DMAX>::a, DMAX, ES>(ad, tab, Zs, Acc, r, qm2, m, d, St, Lm);
   if (d == Fast<DMAX>::b)
-    return check_body<G, FORM, Fast<DMAX>::b, DMAX, ES, SIDX>(c, r, qm2, m, d, Zs, Acc, St, Lm, sidx);
-  return check_body<G, FORM, 0, DMAX, ES, SIDX>(c, r, qm2, m, d, Zs, Acc, St, Lm, sidx);
-}
-
-template <int G, int DMAX, bool SIDX>
-__device__ __forceinline__ uint32_t row_parity_h2(const DevCode& c, const uint16_t* __restrict__ sidx,
-                                                  const uint32_t* __restrict__ Zs, int m) {
-  return row_parity_body<G, 0, DMAX, SIDX>(c, sidx, Zs, m, c.deg(m));
+    return check_body<G, FORM, Fast<DMAX>::b, DMAX, ES>(ad, tab, Zs, Acc, r, qm2, m, d, St, Lm);
+  return check_body<G, FORM, 0, DMAX, ES>(ad, tab, Zs, Acc, r, qm2, m, d, St, Lm);
 }
 
 __device__ __forceinline__ int32_t q0v(const int8_t* __restrict__ llr, int32_t N, int32_t f, int32_t F, int n) {
@@ -291,6 +95,7 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
   const int N8 = (N + 7) >> 3;
   const uint32_t qm2 = ints_to_h2(r.qm, r.qm);
   const H2Rule hr = make_h2rule(r);
+  const LocalAddr<G, SIDX> ad{c.M};
   if constexpr (SIDX) {
     // the column table is the same for every frame group: copy it once
     const int words = (c.ell_w * M) >> 1;
@@ -332,7 +137,7 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
       const int kp = k & 1;
       uint32_t fail = 0;
       for (int m = tid; m < M; m += nt)
-        fail |= check_update_h2<G, FORM, DMAX, ES, SIDX>(c, hr, qm2, m, Zs, Acc, St, Lm, sidx);
+        fail |= check_update_h2<G, FORM, DMAX, ES>(ad, SIDX ? sidx : c.ell16, Zs, Acc, c.rdeg, hr, qm2, m, St, Lm);
       if constexpr (ES) {
         fail = __reduce_or_sync(0xffffffffu, fail);
         if ((tid & 31) == 0 && (fail & act)) atomicOr(&s_fail[kp], fail & act);
@@ -367,7 +172,7 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
 
     if (act != 0u) {
       uint32_t fail = 0;
-      for (int m = tid; m < M; m += nt) fail |= row_parity_h2<G, DMAX, SIDX>(c, sidx, Zs, m);
+      for (int m = tid; m < M; m += nt) fail |= row_parity_body<G, 0, DMAX>(ad, SIDX ? sidx : c.ell16, Zs, m, (int)__ldg(c.rdeg + m));
       fail = __reduce_or_sync(0xffffffffu, fail);
       if ((tid & 31) == 0 && (fail & act)) atomicOr(&s_fail[2], fail & act);
       __syncthreads();

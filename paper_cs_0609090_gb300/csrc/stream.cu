@@ -5,7 +5,9 @@
 // warp -- consecutive frames -- read and atomically update consecutive words):
 //   int8 path, lane = frame pair, exact binary16 arithmetic (see h2ops.cuh):
 //     Zs [N][FP] half2, Acc [N][FP] i32 (lo + 65536 hi, biased like onchip_h2),
-//     state [M][FP] uint4 (Section V) or [E][FP] u16 (per-edge bytes L + 128),
+//     state [M][FP] uint4 (Section V) or [E][FP] u16 (per-edge bytes L + 128
+//     by CSR edge; the region is sized for ell_w M edge slots, the layout of
+//     h2s_rows_ell's per-edge form),
 //     q0 [N][FP] u16 (int8 pair), act/fail [2][FP] u32 bit masks, iters [2 FP]
 //   float path, lane = frame:
 //     Z [N][FL] f32, Acc [N][FL] f32, state [M][FL] uint4 {A, B, n~, signs} or
@@ -17,7 +19,7 @@
 // floating-point atomics, so its rounding depends on the order of the additions.
 #include <algorithm>
 
-#include "h2ops.cuh"
+#include "h2_body.cuh"
 #include "kernels.h"
 
 namespace ldpc {
@@ -201,6 +203,64 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) h2s_rows(const DevCode c,
   uint32_t fail = 0;
   const int m1 = min(m0 + kRowsPerWarp, c.M);
   for (int m = m0; m < m1; ++m) fail |= h2s_check<FORM, ES>(c, r, qm2, m, p, s);
+  if (ES && fail) atomicOr(s.fail + cur * s.FP + p, fail);
+}
+
+// The frame-pair streaming layout as an addressing policy of the shared check
+// body (h2_body.cuh): handles are 32-bit element offsets n FP, the lane's own
+// pair p is folded into the base pointers, and the column index of a position
+// (the same for the whole warp) comes from the degree-sorted edge-slot table.
+template <bool WIDE>
+struct StreamAddr {
+  using H = uint32_t;
+  int M;
+  uint32_t FP;
+  const uint16_t* __restrict__ t16;
+  const int32_t* __restrict__ t32;
+  __device__ __forceinline__ H at(const uint16_t*, const uint32_t*, int j, int m) const {
+    const int n = WIDE ? __ldg(t32 + j * M + m) : (int)__ldg(t16 + j * M + m);
+    return (uint32_t)n * FP;
+  }
+  __device__ __forceinline__ void load(const uint32_t* __restrict__ Zs, H h, uint32_t (&w)[1]) const { w[0] = Zs[h]; }
+  __device__ __forceinline__ void add(int32_t* __restrict__ Acc, H h, int, int32_t v) const { atomicAdd(Acc + h, v); }
+  __device__ __forceinline__ uint32_t st(int m) const { return (uint32_t)m * FP; }
+  __device__ __forceinline__ uint32_t lm(int j, int m) const { return (uint32_t)(j * M + m) * FP; }
+};
+
+// Row pass with the exact-degree bodies: one warp = kRowsPerWarp consecutive
+// checks of the degree-sorted order for 32 frame pairs.  Per-edge messages are
+// kept per edge slot (j * M + internal check).  Offsets are 32-bit (the host
+// checks N FP and ell_w M FP < 2^32).
+template <int FORM, bool ES, bool WIDE, int MINB>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const DevCode c, const IntRule r, H2S s, int k) {
+  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = s.FP / 32;
+  const int chunk = warp % n_chunks;
+  const int m0 = (warp / n_chunks) * kRowsPerWarp;
+  if (m0 >= c.M) return;
+  const int p = chunk * 32 + lane;
+  const int cur = k & 1;
+  if (__all_sync(0xffffffffu, s.act[cur * s.FP + p] == 0u)) return;
+  const uint32_t qm2 = ints_to_h2(r.qm, r.qm);
+  const H2Rule hr = make_h2rule(r);
+  const StreamAddr<WIDE> ad{c.M, (uint32_t)s.FP, c.ell16, c.ell32};
+  const uint32_t* Zs = s.z + p;
+  int32_t* Acc = s.acc + p;
+  uint4* St = s.st + p;
+  uint16_t* Lm = s.lm + p;
+  uint32_t fail = 0;
+  const int m1 = min(m0 + kRowsPerWarp, c.M);
+  for (int m = m0; m < m1; ++m) {
+    const int d = (int)__ldg(c.rdeg + m);
+    switch (d) {
+      case 6: fail |= check_body<2, FORM, 6, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 7: fail |= check_body<2, FORM, 7, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 14: fail |= check_body<2, FORM, 14, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 15: fail |= check_body<2, FORM, 15, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      default: fail |= check_body<2, FORM, 0, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+    }
+  }
   if (ES && fail) atomicOr(s.fail + cur * s.FP + p, fail);
 }
 
@@ -529,8 +589,19 @@ cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H
   const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
                    L.lanes / 32);
   (void)F;
+  // 32-bit element offsets for the degree-sorted kernel; otherwise the CSR kernel
+  const uint64_t span = std::max((uint64_t)c.N, (uint64_t)c.ell_w * (uint64_t)c.M) * (uint64_t)L.lanes;
+  const bool ell = span < (1ull << 32);
+  // Measured on the N=64800 staircase code (1024 frames, 50 iterations): the
+  // degree-sorted kernel at 4 CTAs per SM is the faster one for the Section V
+  // state (20.3 against 21.0 ms), the CSR kernel for per-edge messages (22.3
+  // against 22.9 ms).  The row pass waits on L2 gathers and atomics, so
+  // occupancy counts more than instruction count (2 CTAs per SM: 26.7 ms).
   for (int k = 1; k <= max_iter; ++k) {
-    h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+    if (FORM == 1 && ell && c.ell16 != nullptr)
+      h2s_rows_ell<FORM, ES, false, 4><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+    else if (FORM == 1 && ell) h2s_rows_ell<FORM, ES, true, 4><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+    else h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
     h2s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k);
   }
   return cudaGetLastError();

@@ -87,6 +87,51 @@ def make_workload(name: str, n_frames: int | None = None, ebn0_db: float | None 
     return w
 
 
+# The uneven eight-code batch decoded in one launch: three (3,6)-regular codes,
+# two quasi-cyclic 24x59 codes (Z = 61, 127) and three staircase codes, each
+# with its family's channel quantization and rule, 30 iterations.
+# (kind, N, code seed, Eb/N0, delta, qc, params)
+_REG = dict(dtype="int8", rule="offset", offset=1, msg_sat=31, max_iter=30, early_stop=1)
+_QC = dict(dtype="int8", rule="offset", offset=2, msg_sat=127, max_iter=30, early_stop=1)
+_IRR = dict(dtype="int8", rule="normalized", norm_num=3, norm_shift=2, norm=0.75, msg_sat=127, max_iter=30,
+            early_stop=1)
+MULTI8 = (("reg36", 1008, 11, 2.0, 0.25, 31, _REG),
+          ("reg36", 2016, 12, 2.0, 0.25, 31, _REG),
+          ("reg36", 4032, 13, 2.0, 0.25, 31, _REG),
+          ("qc", 3599, 22, 2.5, 0.125, 127, _QC),
+          ("qc", 7493, 21, 2.5, 0.125, 127, _QC),
+          ("irr", 16200, 32, 2.0, 0.125, 127, _IRR),
+          ("irr", 32400, 33, 2.0, 0.125, 127, _IRR),
+          ("irr", 64800, 31, 2.0, 0.125, 127, _IRR))
+
+
+def multi8_frame_counts(mean_frames: int = 512, seed: int = 4) -> list:
+    """Frames per code of the eight-code batch: Poisson(mean_frames), seeded."""
+    return [int(x) for x in np.random.default_rng(seed).poisson(mean_frames, size=len(MULTI8))]
+
+
+def make_multi_workload(frames=None, mean_frames: int = 512, seed: int = 4, frame_seed: int = 1,
+                        zero_codeword: bool = False, with_llr: bool = True, codes=None) -> list:
+    """The eight-code batch as a list of Workloads (one per code).  ``frames``:
+    explicit frame counts (default Poisson(mean_frames)); ``codes``: indices
+    into MULTI8 to keep."""
+    counts = multi8_frame_counts(mean_frames, seed) if frames is None else list(frames)
+    out = []
+    for i, (kind, n, cseed, eb, delta, qc, params) in enumerate(MULTI8):
+        if codes is not None and i not in codes:
+            continue
+        c = _code(kind, n, cseed)
+        F = counts[i]
+        w = Workload(f"multi8/{kind}_n{n}", c, eb, delta, qc, dict(params), F)
+        if with_llr:
+            cw = (np.zeros((F, c.n_vars), dtype=np.uint8) if zero_codeword
+                  else _encoder(c).random_codewords(F, seed=(frame_seed * 7919 + 1) * 31 + i))
+            llr = awgn_llr(cw, eb, c.n_info / c.n_vars, seed=(frame_seed * 104729 + 3) * 31 + i)
+            w.codewords, w.llr, w.q0 = cw, llr, quantize(llr, delta, qc)
+        out.append(w)
+    return out
+
+
 _enc_cache: dict = {}
 
 

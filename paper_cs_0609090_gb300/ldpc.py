@@ -27,15 +27,17 @@ LDPC_RULE_PLAIN, LDPC_RULE_OFFSET, LDPC_RULE_NORMALIZED = 0, 1, 2
 DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_F32}
 FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
 RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED}
-LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM = 0, 1, 2, 3
+LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM, LDPC_KERNEL_CLUSTER = range(5)
 KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF,
-           "stream": LDPC_KERNEL_STREAM}
+           "stream": LDPC_KERNEL_STREAM, "cluster": LDPC_KERNEL_CLUSTER}
 
 # Every symbol include/ldpc_gb300.h declares.
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",
            "ldpc_decode_batch", "ldpc_decode_batch_noalloc", "ldpc_code_degree_classes",
            "ldpc_learned_workspace_size", "ldpc_learned_forward", "ldpc_learned_loss", "ldpc_learned_backward",
-           "ldpc_adam_step", "ldpc_awgn_llr_f32", "ldpc_quantize_llr", "ldpc_last_error")
+           "ldpc_adam_step", "ldpc_awgn_llr_f32", "ldpc_quantize_llr", "ldpc_multi_create", "ldpc_multi_destroy",
+           "ldpc_multi_workspace_size", "ldpc_multi_decode", "ldpc_multi_autotune", "ldpc_multi_info",
+           "ldpc_last_error")
 NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -51,6 +53,17 @@ class ldpc_decode_params(ctypes.Structure):
                 ("offset_f32", ctypes.c_float), ("norm_f32", ctypes.c_float),
                 ("msg_sat", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("early_stop", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+
+
+class ldpc_multi_job(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("params", ldpc_decode_params), ("llr", ctypes.c_void_p),
+                ("n_frames", ctypes.c_int32), ("hard_bits", ctypes.c_void_p), ("iters_used", ctypes.c_void_p),
+                ("syndrome_ok", ctypes.c_void_p), ("llr_out", ctypes.c_void_p)]
+
+
+class ldpc_multi_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("team_threads", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("queue", ctypes.c_int32), ("large", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -74,6 +87,14 @@ _lib.ldpc_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, 
 _lib.ldpc_awgn_llr_f32.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]
 _lib.ldpc_quantize_llr.argtypes = [_P, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, _P, _P]
+_lib.ldpc_multi_create.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(ldpc_multi_job), ctypes.c_int32,
+                                   ctypes.POINTER(ldpc_multi_tuning)]
+_lib.ldpc_multi_destroy.argtypes = [_P]
+_lib.ldpc_multi_workspace_size.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+_lib.ldpc_multi_decode.argtypes = [_P, _P, ctypes.c_size_t, _P]
+_lib.ldpc_multi_autotune.argtypes = [_P, _P, ctypes.c_size_t, ctypes.c_int32, _P, ctypes.POINTER(ldpc_multi_tuning),
+                                     ctypes.POINTER(ctypes.c_float)]
+_lib.ldpc_multi_info.argtypes = [_P, ctypes.POINTER(ldpc_multi_tuning), _P, _P, _P, _P, _P]
 _lib.ldpc_last_error.restype = ctypes.c_char_p
 for _f in EXPORTS[:-1]:
     getattr(_lib, _f).restype = ctypes.c_int32
@@ -219,6 +240,51 @@ def ldpc_quantize_llr(llr, n: int, delta: float, qc: int, q, stream=None) -> Non
            "ldpc_quantize_llr")
 
 
+def ldpc_multi_create(jobs, tuning: ldpc_multi_tuning | None = None) -> int:
+    """jobs: a sequence of ldpc_multi_job.  Returns an opaque plan handle."""
+    arr = (ldpc_multi_job * len(jobs))(*jobs)
+    h = _P()
+    _check(_lib.ldpc_multi_create(ctypes.byref(h), arr, len(jobs), ctypes.byref(tuning) if tuning else None),
+           "ldpc_multi_create")
+    return h.value
+
+
+def ldpc_multi_destroy(plan: int) -> None:
+    _check(_lib.ldpc_multi_destroy(_P(plan)), "ldpc_multi_destroy")
+
+
+def ldpc_multi_workspace_size(plan: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib.ldpc_multi_workspace_size(_P(plan), ctypes.byref(out)), "ldpc_multi_workspace_size")
+    return out.value
+
+
+def ldpc_multi_decode(plan: int, workspace, ws_bytes: int, stream=None) -> None:
+    _check(_lib.ldpc_multi_decode(_P(plan), _ptr(workspace), int(ws_bytes), _stream_handle(stream)),
+           "ldpc_multi_decode")
+
+
+def ldpc_multi_autotune(plan: int, workspace, ws_bytes: int, reps: int = 3, stream=None):
+    """Returns (chosen ldpc_multi_tuning, mean ms of the kept shape)."""
+    t = ldpc_multi_tuning()
+    ms = ctypes.c_float()
+    _check(_lib.ldpc_multi_autotune(_P(plan), _ptr(workspace), int(ws_bytes), int(reps), _stream_handle(stream),
+                                    ctypes.byref(t), ctypes.byref(ms)), "ldpc_multi_autotune")
+    return t, ms.value
+
+
+def ldpc_multi_info(plan: int, n_jobs: int) -> dict:
+    t = ldpc_multi_tuning()
+    grid, cluster, smem = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    is_cl = (ctypes.c_int32 * n_jobs)()
+    pairs = (ctypes.c_int32 * n_jobs)()
+    _check(_lib.ldpc_multi_info(_P(plan), ctypes.byref(t), ctypes.byref(grid), ctypes.byref(cluster),
+                                ctypes.byref(smem), is_cl, pairs), "ldpc_multi_info")
+    return {"threads": t.threads, "team_threads": t.team_threads, "cluster": cluster.value, "queue": t.queue,
+            "large": t.large, "grid": grid.value, "smem_bytes": smem.value, "job_is_cluster": list(is_cl),
+            "job_pairs_per_cta": list(pairs)}
+
+
 class Code:
     """Owning wrapper of an ldpc_code handle."""
 
@@ -268,6 +334,60 @@ def decode(code: Code, llr, params: ldpc_decode_params, want_llr: bool = False, 
                                   _ptr(iters), _ptr(ok), _ptr(zo), ws_ptr, int(ws_bytes),
                                   _stream_handle(stream)), "ldpc_decode_batch")
     return bits, iters, ok, zo
+
+
+class MultiBatch:
+    """A plan over several codes with torch-allocated outputs bound to it:
+    ``decode()`` runs every job in one launch (ldpc_multi_decode);
+    ``outputs[j]`` = (hard_bits, iters, ok, llr_out or None) of job j."""
+
+    def __init__(self, codes, llrs, params, want_llr: bool = False, tuning: ldpc_multi_tuning | None = None):
+        import torch
+        self.codes, self.llrs = list(codes), list(llrs)
+        self.params = list(params) if isinstance(params, (list, tuple)) else [params] * len(self.codes)
+        self.outputs = []
+        jobs = []
+        for c, q, p in zip(self.codes, self.llrs, self.params):
+            F, N = q.shape
+            dev = q.device
+            bits = torch.zeros((F, (N + 7) // 8), dtype=torch.uint8, device=dev)
+            iters = torch.zeros(F, dtype=torch.int32, device=dev)
+            ok = torch.zeros(F, dtype=torch.uint8, device=dev)
+            zo = torch.zeros((F, N), dtype=torch.int16, device=dev) if want_llr else None
+            self.outputs.append((bits, iters, ok, zo))
+            jobs.append(ldpc_multi_job(c.handle, p, q.data_ptr(), F, bits.data_ptr(), iters.data_ptr(),
+                                       ok.data_ptr(), zo.data_ptr() if zo is not None else None))
+        self.handle = ldpc_multi_create(jobs, tuning)
+        self.ws_bytes = ldpc_multi_workspace_size(self.handle)
+        dev = self.llrs[0].device
+        self._ws = torch.empty(max(self.ws_bytes, 1) + 256, dtype=torch.uint8, device=dev)
+        self.ws = _P((self._ws.data_ptr() + 255) & ~255) if self.ws_bytes else None
+
+    def decode(self, stream=None) -> None:
+        _check(_lib.ldpc_multi_decode(_P(self.handle), self.ws, int(self.ws_bytes), _stream_handle(stream)),
+               "ldpc_multi_decode")
+
+    def autotune(self, reps: int = 3, stream=None):
+        t = ldpc_multi_tuning()
+        ms = ctypes.c_float()
+        _check(_lib.ldpc_multi_autotune(_P(self.handle), self.ws, int(self.ws_bytes), int(reps),
+                                        _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)),
+               "ldpc_multi_autotune")
+        return t, ms.value
+
+    def info(self) -> dict:
+        return ldpc_multi_info(self.handle, len(self.codes))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ldpc_multi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def unpack_bits(hard_bits: np.ndarray, n_vars: int) -> np.ndarray:

@@ -59,14 +59,19 @@ def test_int8_stream_edge_cases(L, form):
 @pytest.mark.parametrize("form", FORMS_INT)
 @pytest.mark.parametrize("early_stop", [1, 0])
 def test_int8_irregular_64800(L, form, early_stop):
-    """The N=64800 code does not fit one SM: the library picks the streaming kernel."""
-    w = I.make_workload("irr_n64800", n_frames=6, frame_seed=3)
+    """The N=64800 code does not fit one SM: the streaming kernel (the library's
+    choice) and the cluster kernel (8 CTAs, distributed shared memory) both
+    decode it."""
+    w = I.make_workload("irr_n64800", n_frames=7, frame_seed=3)
     p = dict(w.params, early_stop=early_stop)
-    _int(L, w.code, w.q0, form, p, kernel="auto")
-    if early_stop:
-        q = I.noiseless(w.codewords[:2], 127)
-        g = _int(L, w.code, q, form, p, kernel="auto")
-        assert np.all(g["iters"] == 0)
+    h = L.Code.from_inputs(w.code)
+    assert L.ldpc_workspace_size(h.handle, L.make_params(form=form, **p), 7) > 0
+    for kern in ("auto", "cluster"):
+        _int(L, w.code, w.q0, form, p, kernel=kern)
+        if early_stop:
+            q = I.noiseless(w.codewords[:2], 127)
+            g = _int(L, w.code, q, form, p, kernel=kern)
+            assert np.all(g["iters"] == 0)
 
 
 def _f32(L, code, llr, form, rule, lam=0.75, offset=0.0, max_iter=50, early_stop=0, kernel="stream"):
@@ -138,7 +143,7 @@ def test_stream_workspace_contract(L):
     import torch
     w = I.make_workload("irr_n64800", n_frames=2)
     h = L.Code.from_inputs(w.code)
-    params = L.make_params(**w.params)
+    params = L.make_params(kernel="stream", **w.params)
     need = L.ldpc_workspace_size(h.handle, params, 2)
     assert need > 0
     q = torch.from_numpy(w.q0).cuda()
