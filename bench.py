@@ -372,6 +372,8 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half", "stream", "cluster"])
     ap.add_argument("--dtype", default="int8", choices=["int8", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=None,
+                    help="decode this many frames of the workload instead of its batch (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -386,7 +388,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = I.make_workload(args.workload, frame_seed=1 + rank)
+    w = I.make_workload(args.workload, frame_seed=1 + rank, n_frames=args.frames)
     w.params["early_stop"] = 0
     F, N, K = w.n_frames, w.code.n_vars, w.K
     code = ldpc.Code.from_inputs(w.code, device=local)
