@@ -116,7 +116,9 @@ __device__ __forceinline__ uint32_t row_parity_body(const Addr& ad, const uint16
 //       31 - j, so that shifting the word left by j (a running S + S) brings both
 //       to the binary16 sign bits}
 //   Lm  (FORM 0) [ell_w][rows][P] u16: L + 128 per frame (one byte each)
-template <int G, int FORM, int D, int DMAX, bool ES, class Addr>
+//   DELTA: add L^(k) - L^(k-1) instead of L^(k) (an accumulator that holds
+//       Z^(k-1) and is never reset; used by the streaming kernels)
+template <int G, int FORM, int D, int DMAX, bool ES, class Addr, bool DELTA = false>
 __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* __restrict__ tab,
                                                const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
                                                const H2Rule& rule, uint32_t qm2, int m, int d,
@@ -201,9 +203,12 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
     if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
   }
 
-  uint32_t SN[P];
+  uint32_t SN[P], SO[P];
 #pragma unroll
-  for (int p = 0; p < P; ++p) SN[p] = Sn[p];
+  for (int p = 0; p < P; ++p) {
+    SN[p] = Sn[p];
+    if constexpr (DELTA && FORM == 1) SO[p] = S[p];
+  }
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     if (D > 0 || j < d) {
@@ -211,12 +216,33 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
       if constexpr (KEEP) n = col[j];
       else n = ad.at(tab, Zs, j, m);
       uint32_t sv = 0;
+      uint32_t lold = 0;
+      if constexpr (DELTA && FORM == 0) {
+        if constexpr (P == 1) lold = Lm[ad.lm(j, m)];
+        else lold = reinterpret_cast<const uint32_t*>(Lm)[ad.lm(j, m)];
+      }
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const uint32_t msk = heq_mask(In[p], h2c(j));
         const uint32_t L = ((Bn[p] & msk) | (An[p] & ~msk)) ^ (SN[p] & 0x80008000u);
         SN[p] += SN[p];
-        ad.add(Acc, n, p, (int32_t)hadd(L, h2c(1536)));
+        int32_t v = (int32_t)hadd(L, h2c(1536));
+        if constexpr (DELTA) {
+          // the previous message of this position, as in pass 1
+          uint32_t Lo;
+          if constexpr (FORM == 1) {
+            const uint32_t mo = heq_mask(I2[p], h2c(j));
+            Lo = ((B2[p] & mo) | (A2[p] & ~mo)) ^ (SO[p] & 0x80008000u);
+            SO[p] += SO[p];
+          } else {
+            const uint32_t b = (P == 1) ? lold : (lold >> (16 * p));
+            Lo = hfma(__byte_perm(b, 0x58u, 0x4140), h2c(8), 0xE480E480u);
+          }
+          // lane patterns 0x6600 + L: the 32-bit difference is the exact integer
+          // (L - Lo)_lo + 65536 (L - Lo)_hi
+          v -= (int32_t)hadd(Lo, h2c(1536));
+        }
+        ad.add(Acc, n, p, v);
         if constexpr (FORM == 0) {
           const uint32_t hb = hfma(L, 0x30003000u /* 0.125 */, h2c(144));
           sv |= (uint32_t)__byte_perm(hb, 0u, 0x4420) << (16 * p);

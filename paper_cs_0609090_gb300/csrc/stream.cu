@@ -5,17 +5,20 @@
 // warp -- consecutive frames -- read and atomically update consecutive words):
 //   int8 path, lane = frame pair, exact binary16 arithmetic (see h2ops.cuh):
 //     Zs [N][FP] half2, Acc [N][FP] i32 (lo + 65536 hi, biased like onchip_h2),
-//     state [M][FP] uint4 (Section V) or [E][FP] u16 (per-edge bytes L + 128
-//     by CSR edge; the region is sized for ell_w M edge slots, the layout of
-//     h2s_rows_ell's per-edge form),
+//     state [M][FP] uint4 (Section V) or [ell_w M][FP] u16 (per-edge bytes
+//     L + 128 per edge slot j M + m of the degree-sorted table; by CSR edge in
+//     the fallback kernel),
 //     q0 [N][FP] u16 (int8 pair), act/fail [2][FP] u32 bit masks, iters [2 FP]
 //   float path, lane = frame:
 //     Z [N][FL] f32, Acc [N][FL] f32, state [M][FL] uint4 {A, B, n~, signs} or
 //     [E][FL] f32, q0 [N][FL] f32, act/fail [2][FL] u32, iters [FL]
 // Per iteration: a row kernel (one warp = one check for 32 lanes of frames; the
 // check's column indices are warp-uniform loads) then a column kernel that
-// applies the stop rule and resets the accumulator.  The syndrome of x^(k-1) is
-// computed by the row kernel of iteration k.  The float accumulation uses
+// applies the stop rule.  int8: the row kernel adds L^(k) - L^(k-1) to an
+// accumulator that always holds the current posterior (exact integer sums), so
+// the column kernel only converts it for the frames that continue; the CSR
+// fallback adds L^(k) and the column kernel resets the accumulator to Z0.  The
+// syndrome of x^(k-1) is computed by the row kernel of iteration k.  The float accumulation uses
 // floating-point atomics, so its rounding depends on the order of the additions.
 #include <algorithm>
 
@@ -93,7 +96,7 @@ H2S h2s_view(void* ws, const StreamLayout& L) {
 // Z^(0), the biased accumulator and the per-pair flags.  Tile: 64 variables x
 // 32 pairs (64 frames).
 __global__ void __launch_bounds__(256) h2s_init(const DevCode c, const int8_t* __restrict__ llr, int32_t F,
-                                                int32_t max_iter, H2S s) {
+                                                int32_t max_iter, H2S s, int32_t delta) {
   __shared__ int8_t tile[64][65];  // [frame][variable]
   const int n0 = blockIdx.x * 64, p0 = blockIdx.y * 32;
   const int N = c.N;
@@ -111,7 +114,9 @@ __global__ void __launch_bounds__(256) h2s_init(const DevCode c, const int8_t* _
     const size_t o = (size_t)n * s.FP + p;
     s.q0[o] = (uint16_t)(((uint32_t)lo & 0xffu) | (((uint32_t)hi & 0xffu) << 8));
     s.z[o] = ints_to_h2(lo, hi);
-    s.acc[o] = (int32_t)((uint32_t)acc_pack(lo, hi) - (uint32_t)__ldg(c.cdeg + n) * 0x66006600u);
+    // delta accumulation holds Z^(k-1) itself; the reset form holds Z0 minus the
+    // pattern bias of the col_degree(n) messages that will be added
+    s.acc[o] = (int32_t)((uint32_t)acc_pack(lo, hi) - (delta ? 0u : (uint32_t)__ldg(c.cdeg + n) * 0x66006600u));
   }
   if (blockIdx.x == 0) {
     for (int pl = threadIdx.x; pl < 32; pl += blockDim.x) {
@@ -231,7 +236,7 @@ struct StreamAddr {
 // checks of the degree-sorted order for 32 frame pairs.  Per-edge messages are
 // kept per edge slot (j * M + internal check).  Offsets are 32-bit (the host
 // checks N FP and ell_w M FP < 2^32).
-template <int FORM, bool ES, bool WIDE, int MINB>
+template <int FORM, bool ES, bool WIDE, int MINB, bool DELTA>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const DevCode c, const IntRule r, H2S s, int k) {
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -253,12 +258,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
   const int m1 = min(m0 + kRowsPerWarp, c.M);
   for (int m = m0; m < m1; ++m) {
     const int d = (int)__ldg(c.rdeg + m);
+    using A = StreamAddr<WIDE>;
     switch (d) {
-      case 6: fail |= check_body<2, FORM, 6, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 7: fail |= check_body<2, FORM, 7, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 14: fail |= check_body<2, FORM, 14, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 15: fail |= check_body<2, FORM, 15, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      default: fail |= check_body<2, FORM, 0, 16, ES>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 6: fail |= check_body<2, FORM, 6, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 7: fail |= check_body<2, FORM, 7, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 14: fail |= check_body<2, FORM, 14, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 15: fail |= check_body<2, FORM, 15, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      default: fail |= check_body<2, FORM, 0, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
     }
   }
   if (ES && fail) atomicOr(s.fail + cur * s.FP + p, fail);
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
 
 // Stop rule and accumulator reset for every (variable, pair); pair-level flags
 // are advanced by the threads of variable 0.
-template <bool ES>
+template <bool ES, bool DELTA>
 __global__ void __launch_bounds__(256) h2s_cols(const DevCode c, H2S s, int k) {
   const int p = blockIdx.y * 32 + (threadIdx.x & 31);
   const int cur = k & 1, nxt = cur ^ 1;
@@ -278,10 +284,16 @@ __global__ void __launch_bounds__(256) h2s_cols(const DevCode c, H2S s, int k) {
     const size_t o = (size_t)n * s.FP + p;
     const uint32_t zz = acc_to_pair(s.acc[o]);
     const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
-    s.z[o] = (h & sel) | (s.z[o] & ~sel);
-    const uint32_t q = s.q0[o];
-    s.acc[o] = (int32_t)((uint32_t)acc_pack((int32_t)(int8_t)(q & 0xffu), (int32_t)(int8_t)(q >> 8)) -
-                         (uint32_t)__ldg(c.cdeg + n) * 0x66006600u);
+    if constexpr (DELTA) {
+      // the accumulator carries on; only the frames that continue take Z^(k)
+      if (cont == 3u) s.z[o] = h;
+      else if (cont != 0u) s.z[o] = (h & sel) | (s.z[o] & ~sel);
+    } else {
+      s.z[o] = (h & sel) | (s.z[o] & ~sel);
+      const uint32_t q = s.q0[o];
+      s.acc[o] = (int32_t)((uint32_t)acc_pack((int32_t)(int8_t)(q & 0xffu), (int32_t)(int8_t)(q >> 8)) -
+                           (uint32_t)__ldg(c.cdeg + n) * 0x66006600u);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {
     s.act[nxt * s.FP + p] = cont;
@@ -582,27 +594,28 @@ int rows_grid(int M, int lanes) {
   return (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
 }
 
+// Per iteration: the degree-sorted row kernel with delta accumulation and the
+// converting column kernel (delta == true), or the CSR row kernel with the
+// resetting column kernel when 32-bit element offsets do not reach.  Measured
+// on the N=64800 staircase code (1024 frames, 50 iterations): 17.4 / 20.9 ms
+// (Section V / per-edge) with delta accumulation against 20.2 / 22.3 ms for
+// the best resetting kernels; 4 CTAs per SM beat 3 (19.1 / 21.3 ms) and 2.
 template <int FORM, bool ES>
-cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H2S s, int sm_count, int32_t F,
-                    int32_t max_iter, cudaStream_t st) {
+cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H2S s, int sm_count,
+                    int32_t max_iter, bool delta, cudaStream_t st) {
   const int rgrid = rows_grid(c.M, L.lanes);
   const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
                    L.lanes / 32);
-  (void)F;
-  // 32-bit element offsets for the degree-sorted kernel; otherwise the CSR kernel
-  const uint64_t span = std::max((uint64_t)c.N, (uint64_t)c.ell_w * (uint64_t)c.M) * (uint64_t)L.lanes;
-  const bool ell = span < (1ull << 32);
-  // Measured on the N=64800 staircase code (1024 frames, 50 iterations): the
-  // degree-sorted kernel at 4 CTAs per SM is the faster one for the Section V
-  // state (20.3 against 21.0 ms), the CSR kernel for per-edge messages (22.3
-  // against 22.9 ms).  The row pass waits on L2 gathers and atomics, so
-  // occupancy counts more than instruction count (2 CTAs per SM: 26.7 ms).
+  const bool wide = c.ell16 == nullptr;
   for (int k = 1; k <= max_iter; ++k) {
-    if (FORM == 1 && ell && c.ell16 != nullptr)
-      h2s_rows_ell<FORM, ES, false, 4><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
-    else if (FORM == 1 && ell) h2s_rows_ell<FORM, ES, true, 4><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
-    else h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
-    h2s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k);
+    if (delta) {
+      if (wide) h2s_rows_ell<FORM, ES, true, 4, true><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+      else h2s_rows_ell<FORM, ES, false, 4, true><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+      h2s_cols<ES, true><<<cgrid, 256, 0, st>>>(c, s, k);
+    } else {
+      h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+      h2s_cols<ES, false><<<cgrid, 256, 0, st>>>(c, s, k);
+    }
   }
   return cudaGetLastError();
 }
@@ -630,13 +643,16 @@ cudaError_t stream_int8_decode(const DevCode& c, const IntRule& r, int form, con
   // L^(0) = 0: Section V state all zero, per-edge bytes L + 128 = 0x80
   cudaError_t e0 = cudaMemsetAsync(static_cast<char*>(ws) + L.st, form == 1 ? 0 : 0x80, L.q0 - L.st, st);
   if (e0 != cudaSuccess) return e0;
-  h2s_init<<<tgrid, 256, 0, st>>>(c, llr, F, max_iter, s);
+  // the degree-sorted kernels address the state with 32-bit element offsets
+  const uint64_t span = std::max((uint64_t)c.N, (uint64_t)c.ell_w * (uint64_t)c.M) * (uint64_t)L.lanes;
+  const bool delta = span < (1ull << 32);
+  h2s_init<<<tgrid, 256, 0, st>>>(c, llr, F, max_iter, s, delta ? 1 : 0);
   cudaError_t e;
   const bool es = early_stop != 0;
-  if (form == 1) e = es ? h2s_run<1, true>(c, r, L, s, sm_count, F, max_iter, st)
-                        : h2s_run<1, false>(c, r, L, s, sm_count, F, max_iter, st);
-  else e = es ? h2s_run<0, true>(c, r, L, s, sm_count, F, max_iter, st)
-              : h2s_run<0, false>(c, r, L, s, sm_count, F, max_iter, st);
+  if (form == 1) e = es ? h2s_run<1, true>(c, r, L, s, sm_count, max_iter, delta, st)
+                        : h2s_run<1, false>(c, r, L, s, sm_count, max_iter, delta, st);
+  else e = es ? h2s_run<0, true>(c, r, L, s, sm_count, max_iter, delta, st)
+              : h2s_run<0, false>(c, r, L, s, sm_count, max_iter, delta, st);
   if (e != cudaSuccess) return e;
   const int kf = max_iter + 1;
   h2s_final_syndrome<<<rows_grid(c.M, L.lanes), kWarpsPerBlock * 32, 0, st>>>(c, s, kf);
