@@ -37,6 +37,9 @@ struct ldpc_code {
   int32_t n_classes = 0;
   int32_t class_deg[32] = {};       // check degree of each class, ascending
   int32_t ell_w = 0;
+  int32_t n_dc = 0;                 // degree runs of the internal order (0: more than 4)
+  int32_t dc_end[4] = {};
+  int32_t dc_deg[4] = {};
   int sm_count = 0;
   size_t smem_optin = 0;
   ClusterTables ctab[kClusterSizes];

@@ -23,10 +23,22 @@ struct DevCode {
   // slots (j * M + m) of variable n are cslot[cptr[n] .. cptr[n+1]-1].
   const int32_t* __restrict__ cptr;   // [N+1]
   const int32_t* __restrict__ cslot;  // [E]
+  // The internal order sorted by degree as runs: checks [dc_end[i-1], dc_end[i])
+  // have degree dc_deg[i] (n_dc <= 4 runs; otherwise n_dc = 0 and rdeg serves).
+  int32_t n_dc;
+  int32_t dc_end[4];
+  int32_t dc_deg[4];
   __device__ __forceinline__ int col(int j, int m) const {
     return ell16 != nullptr ? (int)__ldg(ell16 + (size_t)j * M + m) : __ldg(ell32 + (size_t)j * M + m);
   }
-  __device__ __forceinline__ int deg(int m) const { return (int)__ldg(rdeg + m); }
+  __device__ __forceinline__ int deg(int m) const {
+    if (n_dc == 0) return (int)__ldg(rdeg + m);
+    int d = dc_deg[0];
+#pragma unroll
+    for (int i = 1; i < 4; ++i)
+      if (i < n_dc && m >= dc_end[i - 1]) d = dc_deg[i];
+    return d;
+  }
 };
 
 // Magnitude modification of Section III applied to integer magnitudes:

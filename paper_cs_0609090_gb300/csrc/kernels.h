@@ -19,6 +19,7 @@ struct OnchipPlan {
   int n_groups = 0;
   int dmax = 0;         // unrolled row-degree bound (packed-half kernel)
   bool sidx = false;    // column table copied into shared memory
+  bool rset = false;    // accumulator reset values kept in shared memory
 };
 
 // Fills *plan for an int8 decode (form: 0 fixed, 1 one-bit).  Returns false if

@@ -49,6 +49,11 @@ ldpc::DevCode view(const ldpc_code* c) {
   v.ell_w = c->ell_w;
   v.cptr = c->d_cptr;
   v.cslot = c->d_cslot;
+  v.n_dc = c->n_dc;
+  for (int i = 0; i < 4; ++i) {
+    v.dc_end[i] = c->dc_end[i];
+    v.dc_deg[i] = c->dc_deg[i];
+  }
   return v;
 }
 
@@ -257,6 +262,16 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   c->ell_w = max_row;
   c->n_classes = n_cls;
   for (int32_t q = 0; q < n_cls; ++q) c->class_deg[q] = cls_deg[q];
+  // the degree-sorted internal order as runs of equal degree
+  if (n_cls <= 4) {
+    c->n_dc = n_cls;
+    int32_t end = 0;
+    for (int32_t q = 0; q < n_cls; ++q) {
+      while (end < n_checks && rdeg[(size_t)end] == cls_deg[q]) ++end;
+      c->dc_end[q] = end;
+      c->dc_deg[q] = cls_deg[q];
+    }
+  }
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
   c->sm_count = v;

@@ -34,18 +34,21 @@ constexpr int kThreadsMax = 1024;
 __host__ __device__ constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct H2Layout {
-  size_t zs, acc, st, idx, total;
+  size_t zs, acc, st, idx, rs, total;
 };
 // E here is the number of edge slots, ell_w * M.  With sidx the edge-slot-major
-// column table (uint16) is copied into shared memory once per CTA.
-__host__ __device__ inline H2Layout h2_layout(int N, int M, int E, int G, int form, bool sidx) {
+// column table (uint16) is copied into shared memory once per CTA; with rset
+// the accumulator's reset value (Z0 minus the message bias) is kept per
+// variable and frame pair for the frame group.
+__host__ __device__ inline H2Layout h2_layout(int N, int M, int E, int G, int form, bool sidx, bool rset = false) {
   const size_t P = (size_t)G / 2;
   H2Layout L;
   L.zs = 0;
   L.acc = a16((size_t)N * P * 4);
   L.st = L.acc + a16((size_t)N * P * 4);
   L.idx = L.st + a16(form == 1 ? (size_t)M * P * 16 : (size_t)E * P * 2);
-  L.total = L.idx + (sidx ? a16((size_t)E * 2) : 0);
+  L.rs = L.idx + (sidx ? a16((size_t)E * 2) : 0);
+  L.total = L.rs + (rset ? a16((size_t)N * P * 4) : 0);
   return L;
 }
 
@@ -62,6 +65,8 @@ __device__ __forceinline__ uint32_t check_update_h2(const Addr& ad, const uint16
                                                     const uint8_t* __restrict__ rdeg, const H2Rule& r,
                                                     uint32_t qm2, int m, uint4* __restrict__ St,
                                                     uint16_t* __restrict__ Lm) {
+  // (a load of the degree byte measured faster here than deriving it from the
+  // degree runs, which the streaming kernels use)
   const int d = (int)__ldg(rdeg + m);
   if (d == Fast<DMAX>::a)
     return check_body<G, FORM, Fast<DMAX>::a, DMAX, ES>(ad, tab, Zs, Acc, r, qm2, m, d, St, Lm);
@@ -74,7 +79,7 @@ __device__ __forceinline__ int32_t q0v(const int8_t* __restrict__ llr, int32_t N
   return f < F ? (int32_t)__ldg(llr + (size_t)f * N + n) : 0;
 }
 
-template <int G, int FORM, int DMAX, bool ES, bool SIDX>
+template <int G, int FORM, int DMAX, bool ES, bool SIDX, bool RSET>
 __global__ void __launch_bounds__(kThreadsMax, 1)
 onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ llr, int32_t F, int32_t max_iter,
                  uint8_t* __restrict__ bits, int32_t* __restrict__ iters, uint8_t* __restrict__ okf,
@@ -82,7 +87,8 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
   constexpr int P = G / 2;
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = c.N, M = c.M;
-  const H2Layout Ly = h2_layout(N, M, c.ell_w * M, G, FORM, SIDX);
+  const H2Layout Ly = h2_layout(N, M, c.ell_w * M, G, FORM, SIDX, RSET);
+  int32_t* Rs = reinterpret_cast<int32_t*>(smem + Ly.rs);
   uint32_t* Zs = reinterpret_cast<uint32_t*>(smem + Ly.zs);
   int32_t* Acc = reinterpret_cast<int32_t*>(smem + Ly.acc);
   uint4* St = reinterpret_cast<uint4*>(smem + Ly.st);
@@ -118,7 +124,9 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
       for (int p = 0; p < P; ++p) {
         const int32_t lo = q0v(llr, N, f0 + 2 * p, F, n), hi = q0v(llr, N, f0 + 2 * p + 1, F, n);
         w[p] = ints_to_h2(lo, hi);
-        Acc[(size_t)n * P + p] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+        const int32_t reset = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+        Acc[(size_t)n * P + p] = reset;
+        if constexpr (RSET) Rs[(size_t)n * P + p] = reset;
       }
       st_pairs<G>(Zs, n, w);
     }
@@ -146,7 +154,6 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
       const uint32_t stop = ES ? (act & ~s_fail[kp]) : 0u;
       const uint32_t cont = act & ~stop;
       for (int n = tid; n < N; n += nt) {
-        const uint32_t bias = (uint32_t)__ldg(c.cdeg + n) * 0x66006600u;
         uint32_t w[P];
         ld_pairs<G>(Zs, n, w);
 #pragma unroll
@@ -156,8 +163,13 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
           const uint32_t sel = (((cont >> (2 * p)) & 1u) ? 0x0000ffffu : 0u) |
                                (((cont >> (2 * p + 1)) & 1u) ? 0xffff0000u : 0u);
           w[p] = (h & sel) | (w[p] & ~sel);
-          const int32_t lo = q0v(llr, N, f0 + 2 * p, F, n), hi = q0v(llr, N, f0 + 2 * p + 1, F, n);
-          Acc[(size_t)n * P + p] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+          if constexpr (RSET) {
+            Acc[(size_t)n * P + p] = Rs[(size_t)n * P + p];
+          } else {
+            const uint32_t bias = (uint32_t)__ldg(c.cdeg + n) * 0x66006600u;
+            const int32_t lo = q0v(llr, N, f0 + 2 * p, F, n), hi = q0v(llr, N, f0 + 2 * p + 1, F, n);
+            Acc[(size_t)n * P + p] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+          }
         }
         st_pairs<G>(Zs, n, w);
       }
@@ -207,11 +219,11 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
   }
 }
 
-template <int G, int FORM, int DMAX, bool ES, bool SIDX>
+template <int G, int FORM, int DMAX, bool ES, bool SIDX, bool RSET>
 cudaError_t h2_launch_t(const DevCode& c, const IntRule& r, OnchipPlan& plan, int sm_count, const int8_t* llr,
                         int32_t F, int32_t max_iter, uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout,
                         cudaStream_t stream, bool occupancy_only) {
-  auto kern = onchip_h2_kernel<G, FORM, DMAX, ES, SIDX>;
+  auto kern = onchip_h2_kernel<G, FORM, DMAX, ES, SIDX, RSET>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -229,11 +241,17 @@ template <int G, int FORM, int DMAX>
 cudaError_t h2_dispatch_es(bool es, const DevCode& c, const IntRule& r, OnchipPlan& plan, int sm_count,
                            const int8_t* llr, int32_t F, int32_t max_iter, uint8_t* bits, int32_t* iters,
                            uint8_t* ok, int16_t* zout, cudaStream_t stream, bool occ) {
+  if (plan.sidx && plan.rset)
+    return es ? h2_launch_t<G, FORM, DMAX, true, true, true>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ)
+              : h2_launch_t<G, FORM, DMAX, false, true, true>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ);
   if (plan.sidx)
-    return es ? h2_launch_t<G, FORM, DMAX, true, true>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ)
-              : h2_launch_t<G, FORM, DMAX, false, true>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ);
-  return es ? h2_launch_t<G, FORM, DMAX, true, false>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ)
-            : h2_launch_t<G, FORM, DMAX, false, false>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ);
+    return es ? h2_launch_t<G, FORM, DMAX, true, true, false>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ)
+              : h2_launch_t<G, FORM, DMAX, false, true, false>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ);
+  if (plan.rset)
+    return es ? h2_launch_t<G, FORM, DMAX, true, false, true>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ)
+              : h2_launch_t<G, FORM, DMAX, false, false, true>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ);
+  return es ? h2_launch_t<G, FORM, DMAX, true, false, false>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ)
+            : h2_launch_t<G, FORM, DMAX, false, false, false>(c, r, plan, sm_count, llr, F, max_iter, bits, iters, ok, zout, stream, occ);
 }
 
 }  // namespace
@@ -263,10 +281,13 @@ bool onchip_h2_plan(const DevCode& c, int form, int32_t n_frames, int sm_count, 
       if (fits(g, false)) { G = g; break; }
   if (G == 0) return false;
   while (G > 2 && (int64_t)n_frames < (int64_t)sm_count * G) G /= 2;
+  // the accumulator reset values in shared memory too, when they fit
+  const bool rset = h2_layout(c.N, c.M, c.ell_w * c.M, G, form, sidx, true).total + static_smem <= smem_optin;
   plan->G = G;
   plan->sidx = sidx;
+  plan->rset = rset;
   plan->dmax = max_row_deg <= 8 ? 8 : 16;
-  plan->smem = h2_layout(c.N, c.M, c.ell_w * c.M, G, form, sidx).total;
+  plan->smem = h2_layout(c.N, c.M, c.ell_w * c.M, G, form, sidx, rset).total;
   int threads = ((c.M + 31) / 32) * 32;
   threads = threads > kThreadsMax ? kThreadsMax : (threads < 128 ? 128 : threads);
   plan->threads = threads;

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
   uint32_t fail = 0;
   const int m1 = min(m0 + kRowsPerWarp, c.M);
   for (int m = m0; m < m1; ++m) {
-    const int d = (int)__ldg(c.rdeg + m);
+    const int d = c.deg(m);
     using A = StreamAddr<WIDE>;
     switch (d) {
       case 6: fail |= check_body<2, FORM, 6, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
