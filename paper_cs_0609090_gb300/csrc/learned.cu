@@ -16,7 +16,8 @@
 //                              dLoss/du for the check (ping-pong)
 //   part  [tasks][C] f32       per-task partial sums of dLoss/dbeta (summed in a
 //                              fixed order: the gradient is deterministic)
-//   lpart [blocks] f32         per-block partial sums of the loss
+//   lpart [blocks] f32         per-block partial sums of the loss; also the
+//                              staged class sums of the offset gradient
 //
 // Backward through iteration k (the forward quantities are recomputed from the
 // checkpoints Z^(k-1), S^(k-1) rather than stored):
@@ -271,20 +272,46 @@ __global__ void __launch_bounds__(kLWarps * 32) lb_rows(const DevCode c, const u
   }
 }
 
-// dbeta[k-1][c] = sum over tasks of part[task][c], in a fixed order.
-__global__ void __launch_bounds__(256) lb_reduce(const float* __restrict__ part, int tasks, int C,
-                                                 float* __restrict__ out) {
-  __shared__ float sm[256];
-  const int cls = blockIdx.x;
-  float s = 0.f;
-  for (int t = threadIdx.x; t < tasks; t += blockDim.x) s += part[(size_t)t * C + cls];
+// dbeta[k-1][c] = sum over tasks of part[task][c], in a fixed order: block b
+// sums the tasks [b T / nb, (b+1) T / nb) of every class into stage[b][c]
+// (lb_reduce1), then one block sums stage[0..nb) (lb_reduce2).  The partition
+// and both in-block trees are fixed, so the result does not depend on timing.
+constexpr int kReduceBlocks = 256;
+
+__device__ __forceinline__ float block_sum(float s, float* sm) {
   sm[threadIdx.x] = s;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[cls] = sm[0];
+  const float r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) lb_reduce1(const float* __restrict__ part, int tasks, int C,
+                                                  float* __restrict__ stage) {
+  __shared__ float sm[256];
+  const int t0 = (int)((int64_t)tasks * blockIdx.x / gridDim.x);
+  const int t1 = (int)((int64_t)tasks * (blockIdx.x + 1) / gridDim.x);
+  for (int cls = 0; cls < C; ++cls) {
+    float s = 0.f;
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) s += part[(size_t)t * C + cls];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) stage[blockIdx.x * C + cls] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) lb_reduce2(const float* __restrict__ stage, int nb, int C,
+                                                  float* __restrict__ out) {
+  __shared__ float sm[256];
+  for (int cls = 0; cls < C; ++cls) {
+    float s = 0.f;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += stage[b * C + cls];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) out[cls] = s;
+  }
 }
 
 __global__ void __launch_bounds__(256) zero_f(float* __restrict__ p, size_t n) {
@@ -469,7 +496,9 @@ cudaError_t learned_backward(const DevCode& c, const uint8_t* rclass, int C, int
     const uint4* dun = (k == K) ? nullptr : v.dub((k + 1) & 1);
     uint4* duc = v.dub(k & 1);
     lb_rows<<<rb, kLWarps * 32, 0, st>>>(c, rclass, beta, v, k, dzk, dun, duc, dzp, F);
-    lb_reduce<<<C, 256, 0, st>>>(v.part, L.tasks, C, dbeta + (size_t)(k - 1) * C);
+    // stage partials in the loss-partials buffer (4096 floats >= kReduceBlocks * C)
+    lb_reduce1<<<kReduceBlocks, 256, 0, st>>>(v.part, L.tasks, C, v.lpart);
+    lb_reduce2<<<1, 256, 0, st>>>(v.lpart, kReduceBlocks, C, dbeta + (size_t)(k - 1) * C);
   }
   return cudaGetLastError();
 }
