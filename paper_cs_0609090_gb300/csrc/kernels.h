@@ -74,14 +74,17 @@ struct MultiJob {
   uint8_t* ok;
   int16_t* zout;
   uint32_t tab_bytes, slot_bytes, acc_off, st_off;  // shared-memory layout
+  uint32_t rs_off;  // local jobs: offset of the accumulator reset values in a slot (0: none)
 };
 struct MultiParams {
   int32_t n_jobs, n_cjobs, n_citems, n_litems, cs;
   int32_t* counters;  // [2] zero before the launch, or nullptr: round-robin items
   MultiJob job[kMultiMaxJobs];
 };
-// Bytes of one local pair slot (Zs, Acc, St or Lm) and its offsets.
-size_t multi_local_slot_bytes(int N, int M, int ell_w, int form, size_t* acc_off, size_t* st_off);
+// Bytes of one local pair slot (Zs, Acc, St or Lm, and with rset the
+// accumulator reset values) and its offsets.
+size_t multi_local_slot_bytes(int N, int M, int ell_w, int form, size_t* acc_off, size_t* st_off,
+                              bool rset = false, size_t* rs_off = nullptr);
 // Launches (max_grid == nullptr) or reports the persistent grid of a shape.
 cudaError_t multi_launch(int form, bool es, const MultiParams& mp, int threads, size_t smem, int grid,
                          cudaStream_t st, int* max_grid);

@@ -188,9 +188,11 @@ ldpc_status build(const std::vector<JobIn>& in, int form, const ldpc_multi_tunin
       b.pairs_per_cta[j] = 1;
       order.push_back({(int)j, true, pair_cost});
     } else {
-      size_t acc_off, st_off;
-      const size_t slot = ldpc::multi_local_slot_bytes(c->N, c->M, c->ell_w, form, &acc_off, &st_off);
+      size_t acc_off, st_off, rs_off;
       const size_t tb = a16((size_t)c->ell_w * c->M * 2);
+      // the accumulator reset values join the slot when one slot still fits
+      const bool rset = tb + ldpc::multi_local_slot_bytes(c->N, c->M, c->ell_w, form, nullptr, nullptr, true) <= budget;
+      const size_t slot = ldpc::multi_local_slot_bytes(c->N, c->M, c->ell_w, form, &acc_off, &st_off, rset, &rs_off);
       int want = std::min(ldpc::kMultiMaxSub, std::max(1, T / tt));
       while (want > 1 && want / 2 >= m.n_pairs) want /= 2;  // no more slots than pairs
       int sub = want;
@@ -206,6 +208,7 @@ ldpc_status build(const std::vector<JobIn>& in, int form, const ldpc_multi_tunin
       m.slot_bytes = (uint32_t)slot;
       m.acc_off = (uint32_t)acc_off;
       m.st_off = (uint32_t)st_off;
+      m.rs_off = (uint32_t)rs_off;
       order.push_back({(int)j, false, pair_cost * sub});
     }
   }

@@ -120,6 +120,8 @@ __device__ void decode_pair(const MultiJob& jb, int pair, unsigned char* smem, M
   int32_t* Acc = reinterpret_cast<int32_t*>(base + jb.acc_off);
   uint4* St = reinterpret_cast<uint4*>(base + jb.st_off);
   uint16_t* Lm = reinterpret_cast<uint16_t*>(base + jb.st_off);
+  int32_t* Rs = reinterpret_cast<int32_t*>(base + jb.rs_off);
+  const bool rset = !CL && jb.rs_off != 0u;
   const int v0 = CL ? (int)rank * jb.ns : 0;
   const int nv = CL ? max(0, min(N - v0, jb.ns)) : N;
   const int rows = CL ? __ldg(jb.rows + rank) : jb.M;
@@ -152,7 +154,9 @@ __device__ void decode_pair(const MultiJob& jb, int pair, unsigned char* smem, M
     const uint32_t bias = (uint32_t)__ldg(jb.cdeg + n) * 0x66006600u;
     const int32_t lo = q0v(jb.llr, N, f0, F, n), hi = q0v(jb.llr, N, f0 + 1, F, n);
     Zs[i] = ints_to_h2(lo, hi);
-    Acc[i] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+    const int32_t reset = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+    Acc[i] = reset;
+    if (rset) Rs[i] = reset;
   }
   if constexpr (FORM == 1) {
     for (int i = tid; i < rows; i += nt) St[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -183,13 +187,17 @@ __device__ void decode_pair(const MultiJob& jb, int pair, unsigned char* smem, M
     const uint32_t cont = act & ~stop;
     const uint32_t sel = ((cont & 1u) ? 0x0000ffffu : 0u) | ((cont & 2u) ? 0xffff0000u : 0u);
     for (int i = tid; i < nv; i += nt) {
-      const int n = v0 + i;
-      const uint32_t bias = (uint32_t)__ldg(jb.cdeg + n) * 0x66006600u;
       const uint32_t zz = acc_to_pair(Acc[i]);
       const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
       Zs[i] = (h & sel) | (Zs[i] & ~sel);
-      const int32_t lo = q0v(jb.llr, N, f0, F, n), hi = q0v(jb.llr, N, f0 + 1, F, n);
-      Acc[i] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+      if (rset) {
+        Acc[i] = Rs[i];
+      } else {
+        const int n = v0 + i;
+        const uint32_t bias = (uint32_t)__ldg(jb.cdeg + n) * 0x66006600u;
+        const int32_t lo = q0v(jb.llr, N, f0, F, n), hi = q0v(jb.llr, N, f0 + 1, F, n);
+        Acc[i] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+      }
     }
     if (es) {
       if (tid < 2 && ((stop >> tid) & 1u)) sh.iters[slot][tid] = k - 1;
@@ -389,12 +397,14 @@ cudaError_t multi_launch_t(const MultiParams& mp, int threads, size_t smem, int 
 
 }  // namespace
 
-size_t multi_local_slot_bytes(int N, int M, int ell_w, int form, size_t* acc_off, size_t* st_off) {
+size_t multi_local_slot_bytes(int N, int M, int ell_w, int form, size_t* acc_off, size_t* st_off, bool rset,
+                              size_t* rs_off) {
   const size_t zs = ((size_t)N * 4 + 15) & ~size_t(15);
   const size_t st = form == 1 ? (size_t)M * 16 : (((size_t)ell_w * M * 2 + 15) & ~size_t(15));
   if (acc_off) *acc_off = zs;
   if (st_off) *st_off = 2 * zs;
-  return 2 * zs + st;
+  if (rs_off) *rs_off = rset ? 2 * zs + st : 0;
+  return 2 * zs + st + (rset ? zs : 0);
 }
 
 cudaError_t multi_launch(int form, bool es, const MultiParams& mp, int threads, size_t smem, int grid,

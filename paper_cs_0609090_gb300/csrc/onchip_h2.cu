@@ -153,16 +153,23 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
       __syncthreads();
       const uint32_t stop = ES ? (act & ~s_fail[kp]) : 0u;
       const uint32_t cont = act & ~stop;
+      // without early stop every valid frame continues; the lanes of a missing
+      // frame (an odd batch) hold values nobody reads
+      const bool all = !ES || cont == (1u << G) - 1u;
       for (int n = tid; n < N; n += nt) {
         uint32_t w[P];
-        ld_pairs<G>(Zs, n, w);
+        if (!all) ld_pairs<G>(Zs, n, w);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const uint32_t zz = acc_to_pair(Acc[(size_t)n * P + p]);
           const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
-          const uint32_t sel = (((cont >> (2 * p)) & 1u) ? 0x0000ffffu : 0u) |
-                               (((cont >> (2 * p + 1)) & 1u) ? 0xffff0000u : 0u);
-          w[p] = (h & sel) | (w[p] & ~sel);
+          if (all) {
+            w[p] = h;
+          } else {
+            const uint32_t sel = (((cont >> (2 * p)) & 1u) ? 0x0000ffffu : 0u) |
+                                 (((cont >> (2 * p + 1)) & 1u) ? 0xffff0000u : 0u);
+            w[p] = (h & sel) | (w[p] & ~sel);
+          }
           if constexpr (RSET) {
             Acc[(size_t)n * P + p] = Rs[(size_t)n * P + p];
           } else {
