@@ -63,6 +63,11 @@ struct LocalAddr {
   __device__ __forceinline__ int lm(int j, int m) const { return j * M + m; }
 };
 
+// (a b) >> 32 + c on 32-bit unsigned operands.
+__device__ __forceinline__ uint32_t umad_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d; asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c)); return d;
+}
+
 // |x| of both halves (an operand modifier of the instruction that consumes it).
 __device__ __forceinline__ uint32_t hab(uint32_t a) {
   uint32_t d; asm("abs.f16x2 %0, %1;" : "=r"(d) : "r"(a)); return d;
@@ -177,7 +182,10 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
         }
         const uint32_t u = hsub(w[p], L);
         if constexpr (ES) Y[p] ^= dec_bits(w[p]);
-        NEG[p] |= (u >> j) & (0x80008000u >> j);  // sign of u_j at bit 15 - j / 31 - j
+        // sign of u_j at bit 15 - j / 31 - j: the high word of (u & signs) 2^(32-j)
+        // added to NEG (the bits are disjoint), one multiply-add on the FMA pipe
+        if (j == 0) NEG[p] = u & 0x80008000u;
+        else NEG[p] = umad_hi(u & 0x80008000u, 1u << (32 - j), NEG[p]);
         const uint32_t key = hfma(hmin(hab(u), qm2), h2c(16), h2c(j));
         K2[p] = hmin(K2[p], hmax(K1[p], key));
         K1[p] = hmin(K1[p], key);
