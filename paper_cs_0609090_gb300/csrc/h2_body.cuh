@@ -145,14 +145,17 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
       S[p] = s.w;
     }
   }
-  uint32_t K1[P], K2[P], NEG[P], Y[P], SR[P];
+  uint32_t K1[P], K2[P], NEG[P], Y[P], SR[P], D2[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     K1[p] = h2c(2048);
     K2[p] = h2c(2048);
     NEG[p] = 0;
     Y[p] = 0;
-    if constexpr (FORM == 1) SR[p] = S[p];
+    if constexpr (FORM == 1) {
+      SR[p] = S[p];
+      D2[p] = hsub(B2[p], A2[p]);
+    }
   }
   H col[KEEP ? NJ : 1];
 #pragma unroll
@@ -171,9 +174,9 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
       for (int p = 0; p < P; ++p) {
         uint32_t L;
         if constexpr (FORM == 1) {
-          // f(A, B, n, n~) and the stored sign s_mn on the binary16 sign bit
-          const uint32_t msk = heq_mask(I2[p], h2c(j));
-          L = ((B2[p] & msk) | (A2[p] & ~msk)) ^ (SR[p] & 0x80008000u);
+          // f(A, B, n, n~) = A + (B - A) [j = n~] (exact: small integers), and the
+          // stored sign s_mn on the binary16 sign bit
+          L = hfma(D2[p], heq_one(I2[p], h2c(j)), A2[p]) ^ (SR[p] & 0x80008000u);
           SR[p] += SR[p];
         } else {
           // byte L + 128 -> binary16 128 + (L + 128)/8 -> 8 h - 1152 = L
@@ -211,10 +214,11 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
     if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
   }
 
-  uint32_t SN[P], SO[P];
+  uint32_t SN[P], SO[P], Dn[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     SN[p] = Sn[p];
+    Dn[p] = hsub(Bn[p], An[p]);
     if constexpr (DELTA && FORM == 1) SO[p] = S[p];
   }
 #pragma unroll
@@ -231,16 +235,14 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
       }
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const uint32_t msk = heq_mask(In[p], h2c(j));
-        const uint32_t L = ((Bn[p] & msk) | (An[p] & ~msk)) ^ (SN[p] & 0x80008000u);
+        const uint32_t L = hfma(Dn[p], heq_one(In[p], h2c(j)), An[p]) ^ (SN[p] & 0x80008000u);
         SN[p] += SN[p];
         int32_t v = (int32_t)hadd(L, h2c(1536));
         if constexpr (DELTA) {
           // the previous message of this position, as in pass 1
           uint32_t Lo;
           if constexpr (FORM == 1) {
-            const uint32_t mo = heq_mask(I2[p], h2c(j));
-            Lo = ((B2[p] & mo) | (A2[p] & ~mo)) ^ (SO[p] & 0x80008000u);
+            Lo = hfma(D2[p], heq_one(I2[p], h2c(j)), A2[p]) ^ (SO[p] & 0x80008000u);
             SO[p] += SO[p];
           } else {
             const uint32_t b = (P == 1) ? lold : (lold >> (16 * p));

@@ -41,6 +41,10 @@ __device__ __forceinline__ uint32_t habs(uint32_t a) { return a & 0x7fff7fffu; }
 __device__ __forceinline__ uint32_t heq_mask(uint32_t a, uint32_t b) {
   uint32_t d; asm("set.eq.u32.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b)); return d;
 }
+// 1.0 where the halves are equal, 0.0 elsewhere (binary16 pair).
+__device__ __forceinline__ uint32_t heq_one(uint32_t a, uint32_t b) {
+  uint32_t d; asm("set.eq.f16x2.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b)); return d;
+}
 
 // Exact conversions between int pairs (|v| < 2^22) and half2 (|v| <= 2048).
 __device__ __forceinline__ uint32_t ints_to_h2(int32_t lo, int32_t hi) {
