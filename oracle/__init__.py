@@ -131,6 +131,42 @@ def decode_int(code, q0, *, form="ss_1bit", rule="plain", offset=0, norm_num=3, 
     return r
 
 
+def decode_layered_int(code, q0, layer, *, rule="plain", offset=0, norm_num=3, norm_shift=2, msg_sat=127,
+                       max_iter=20, early_stop=1, want_l=False, threads=0) -> Result:
+    """The single scan of Eq. (3) in a layered schedule: ``layer[m]`` is the
+    layer of check m (checks of one layer share no variable); layers run in
+    increasing order and update the posteriors in place."""
+    lib = _load()
+    if not hasattr(lib, "_lay_ready"):
+        P = ctypes.c_void_p
+        lib.orc_decode_layered_int.argtypes = [P, P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P, P,
+                                               ctypes.c_int32]
+        lib.orc_decode_layered_int.restype = ctypes.c_int
+        lib._lay_ready = True
+    q = np.ascontiguousarray(np.atleast_2d(q0), dtype=np.int32)
+    F, N = q.shape
+    assert N == code.n_vars
+    c, keep = _code_struct(code.row_ptr, code.col_idx, code.n_vars)
+    E = int(keep[0][-1])
+    lay = np.ascontiguousarray(layer, dtype=np.int32)
+    p = _IParams(RULES[rule], int(offset), int(norm_num), int(norm_shift), int(msg_sat),
+                 int(max_iter), int(early_stop))
+    bits = np.zeros((F, N), np.uint8)
+    iters = np.zeros(F, np.int32)
+    ok = np.zeros(F, np.uint8)
+    z = np.zeros((F, N), np.int32)
+    l_out = np.zeros((F, E), np.int32) if want_l else None
+    rc = lib.orc_decode_layered_int(ctypes.byref(c), ctypes.byref(p), _ptr(lay), int(lay.max()) + 1 if lay.size else 1,
+                                    _ptr(q), F, _ptr(bits), _ptr(iters), _ptr(ok), _ptr(z), _ptr(l_out),
+                                    int(threads))
+    if rc != 0:
+        raise ValueError("orc_decode_layered_int rejected its arguments (are the layers column-disjoint?)")
+    r = Result(bits=bits, iters=iters, ok=ok, z=z)
+    if want_l:
+        r["l"] = l_out
+    return r
+
+
 def decode_f64(code, q0, *, form="ss_1bit", rule="normalized", offset=0.0, lam=0.75,
                max_iter=50, early_stop=1, beta_tab=None, want_l=False, want_margin=False,
                threads=0) -> Result:

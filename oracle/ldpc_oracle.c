@@ -231,6 +231,55 @@ static void decode_frame_int(const orc_code *c, const orc_csc *t, const orc_ipar
   }
 }
 
+/* ------------------------------------------- integer, layered, one frame */
+
+/* The single scan of Eq. (3) in a layered schedule (cited in Section I; not
+   the paper's own schedule): the checks are split into layers whose checks
+   share no variable; within an iteration the layers run in order and each
+   check of a layer reads the posteriors as the previous layers left them,
+   computes its new messages from Z_n - L_mn and writes Z_n = (Z_n - L_mn) +
+   L_new_mn in place.  Checks of one layer touch disjoint variables, so their
+   order within the layer does not matter.  The stop rule is the paper's: the
+   decisions of Z after a whole iteration (and before the first). */
+static void decode_frame_layered_int(const orc_code *c, const orc_iparams *p, const int32_t *layer,
+                                     int32_t n_layers, const int32_t *q0, iscratch *w, uint8_t *bits,
+                                     int32_t *iters, uint8_t *ok, int32_t *z_out, int32_t *l_out) {
+  const int32_t N = c->n_vars, M = c->n_checks, E = c->row_ptr[M];
+  const int32_t *rp = c->row_ptr, *ci = c->col_idx;
+  int64_t *Z = w->Z, *L = w->L;
+  for (int32_t n = 0; n < N; ++n) Z[n] = q0[n];
+  for (int32_t e = 0; e < E; ++e) L[e] = 0;
+  int32_t k = 0;
+  int sat = decide_and_check(c, Z, NULL, w->x);
+  if (!(p->early_stop && sat)) {
+    for (k = 1; k <= p->max_iter; ++k) {
+      for (int32_t l = 0; l < n_layers; ++l) {
+        for (int32_t m = 0; m < M; ++m) {
+          if (layer[m] != l) continue;
+          int32_t d = rp[m + 1] - rp[m];
+          for (int32_t j = 0; j < d; ++j) w->u[j] = Z[ci[rp[m] + j]] - L[rp[m] + j];
+          for (int32_t j = 0; j < d; ++j) {
+            int64_t v = check_rule_i(p, w->u, d, j);
+            w->Lraw[j] = sgn_i(v) * modify_i(p, v < 0 ? -v : v);
+          }
+          for (int32_t j = 0; j < d; ++j) {
+            L[rp[m] + j] = w->Lraw[j];
+            Z[ci[rp[m] + j]] = w->u[j] + w->Lraw[j];
+          }
+        }
+      }
+      sat = decide_and_check(c, Z, NULL, w->x);
+      if (p->early_stop && sat) break;
+    }
+    if (k > p->max_iter) k = p->max_iter;
+  }
+  *iters = k;
+  *ok = (uint8_t)sat;
+  for (int32_t n = 0; n < N; ++n) { bits[n] = w->x[n]; z_out[n] = (int32_t)Z[n]; }
+  if (l_out)
+    for (int32_t e = 0; e < E; ++e) l_out[e] = (int32_t)L[e];
+}
+
 /* -------------------------------------------------- double, one frame */
 
 typedef struct {
@@ -352,6 +401,8 @@ typedef struct {
   void *z_out, *l_out;
   int32_t *state_out;
   double *margin_out;
+  const int32_t *layer; /* layered schedule: layer of every check (else NULL) */
+  int32_t n_layers;
   int err;
 } job;
 
@@ -378,7 +429,12 @@ static void *run_job(void *arg) {
       jb->err = -1;
     } else {
       const int32_t *q0 = (const int32_t *)jb->q0;
-      for (int32_t f = jb->f0; f < jb->f1; ++f)
+      for (int32_t f = jb->f0; f < jb->f1 && jb->layer; ++f)
+        decode_frame_layered_int(c, jb->ip, jb->layer, jb->n_layers, q0 + (size_t)f * N, &w,
+                                 jb->bits + (size_t)f * N, jb->iters + f, jb->ok + f,
+                                 (int32_t *)jb->z_out + (size_t)f * N,
+                                 jb->l_out ? (int32_t *)jb->l_out + (size_t)f * E : NULL);
+      for (int32_t f = jb->f0; f < jb->f1 && !jb->layer; ++f)
         decode_frame_int(c, jb->t, jb->ip, jb->form, q0 + (size_t)f * N, &w, jb->bits + (size_t)f * N,
                          jb->iters + f, jb->ok + f, (int32_t *)jb->z_out + (size_t)f * N,
                          jb->l_out ? (int32_t *)jb->l_out + (size_t)f * E : NULL,
@@ -463,6 +519,35 @@ int orc_decode_int(const orc_code *code, const orc_iparams *p, int32_t form, con
   proto.c = code; proto.form = form; proto.is_int = 1; proto.ip = p; proto.q0 = q0;
   proto.bits = bits; proto.iters = iters; proto.ok = ok; proto.z_out = z_out;
   proto.l_out = l_out; proto.state_out = state_out;
+  return run_all(&proto, n_frames, n_threads);
+}
+
+int orc_decode_layered_int(const orc_code *code, const orc_iparams *p, const int32_t *layer, int32_t n_layers,
+                           const int32_t *q0, int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok,
+                           int32_t *z_out, int32_t *l_out, int32_t n_threads) {
+  if (validate(code, ORC_SS_FIXED) || !p || p->max_iter < 0 || n_frames < 0 || !layer || n_layers < 1) return -1;
+  /* every check in a layer; the checks of a layer share no variable */
+  int32_t *owner = (int32_t *)malloc(sizeof(int32_t) * ((size_t)code->n_vars * (size_t)n_layers + 1));
+  if (!owner) return -1;
+  for (size_t i = 0; i < (size_t)code->n_vars * (size_t)n_layers; ++i) owner[i] = -1;
+  int bad = 0;
+  for (int32_t m = 0; m < code->n_checks && !bad; ++m) {
+    if (layer[m] < 0 || layer[m] >= n_layers) { bad = 1; break; }
+    for (int32_t e = code->row_ptr[m]; e < code->row_ptr[m + 1]; ++e) {
+      int32_t *o = &owner[(size_t)layer[m] * code->n_vars + code->col_idx[e]];
+      if (*o >= 0) { bad = 1; break; }
+      *o = m;
+    }
+  }
+  free(owner);
+  if (bad) return -1;
+  if (n_frames == 0) return 0;
+  if (!q0 || !bits || !iters || !ok || !z_out) return -1;
+  job proto;
+  memset(&proto, 0, sizeof proto);
+  proto.c = code; proto.form = ORC_SS_FIXED; proto.is_int = 1; proto.ip = p; proto.q0 = q0;
+  proto.bits = bits; proto.iters = iters; proto.ok = ok; proto.z_out = z_out; proto.l_out = l_out;
+  proto.layer = layer; proto.n_layers = n_layers;
   return run_all(&proto, n_frames, n_threads);
 }
 

@@ -108,6 +108,16 @@ int orc_learned_grad_f64(const orc_code *code, int32_t n_iters, const double *be
                          const uint8_t *targets, int32_t n_frames, double *loss_sum, double *dbeta,
                          double *gap, int32_t n_threads);
 
+/* The single scan of Eq. (3) in a layered schedule: layer[m] in [0, n_layers)
+   gives the layer of check m, the checks of one layer must share no variable
+   (else -1).  Within an iteration the layers run in increasing order; each
+   check updates the posteriors of its variables in place,
+   Z_n = (Z_n - L_mn) + L_new_mn.  Per-edge messages (the Section V state gives
+   the same messages).  Outputs as orc_decode_int (no state_out). */
+int orc_decode_layered_int(const orc_code *code, const orc_iparams *p, const int32_t *layer, int32_t n_layers,
+                           const int32_t *q0, int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok,
+                           int32_t *z_out, int32_t *l_out, int32_t n_threads);
+
 /* Number of threads orc_decode_* would use for n_threads <= 0. */
 int32_t orc_default_threads(void);
 
