@@ -145,19 +145,23 @@ def profiled_traffic(kernel: str, workload: str, form: str):
     return e.get("dram_bytes_per_launch")
 
 
-def cpu_oracle_sample(w, form: str, budget_s: float, max_frames: int):
+def cpu_oracle_sample(w, form: str, budget_s: float, max_frames: int, layers=None):
     """Times the CPU oracle on successive chunks of the workload's frames until
-    ``budget_s`` seconds of wall time or ``max_frames`` frames."""
+    ``budget_s`` seconds of wall time or ``max_frames`` frames (the layered
+    oracle when ``layers`` is given)."""
     import oracle
     p = w.params
     chunk = max(oracle.default_threads() * 2, 8)
     done, t_total = 0, 0.0
+    kw = dict(rule=p["rule"], offset=p.get("offset", 0), norm_num=p.get("norm_num", 3),
+              norm_shift=p.get("norm_shift", 2), msg_sat=p["msg_sat"], max_iter=p["max_iter"], early_stop=0)
     while done < max_frames and t_total < budget_s:
         q = w.q0[done % w.n_frames:][:chunk]
         t0 = time.perf_counter()
-        oracle.decode_int(w.code, q, form=form, rule=p["rule"], offset=p.get("offset", 0),
-                          norm_num=p.get("norm_num", 3), norm_shift=p.get("norm_shift", 2),
-                          msg_sat=p["msg_sat"], max_iter=p["max_iter"], early_stop=0)
+        if layers is not None:
+            oracle.decode_layered_int(w.code, q, layers, **kw)
+        else:
+            oracle.decode_int(w.code, q, form=form, **kw)
         t_total += time.perf_counter() - t0
         done += q.shape[0]
     gbps = done * w.K / t_total / 1e9
@@ -537,6 +541,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half", "stream", "cluster"])
     ap.add_argument("--dtype", default="int8", choices=["int8", "f32"])
+    ap.add_argument("--schedule", default="flooding", choices=["flooding", "layered"],
+                    help="layered: the single scan with column-disjoint layers updating in place")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=None,
                     help="decode this many frames of the workload instead of its batch (profiling runs)")
@@ -563,10 +569,12 @@ def main():
     wp = dict(w.params)
     if args.dtype == "f32":
         wp["dtype"] = "f32"
-    params = ldpc.make_params(form=args.form, kernel=args.kernel, **wp)
+    params = ldpc.make_params(form=args.form, kernel=args.kernel, schedule=args.schedule, **wp)
     ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
     kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel"}.get(args.kernel)
-    if ws_bytes > 0:
+    if args.schedule == "layered":
+        kname = "layered_kernel"
+    elif ws_bytes > 0:
         kname = "f32s_rows" if args.dtype == "f32" else "h2s_rows"
     elif args.form == "two_scan":
         kname = "onchip_twoscan_kernel"
@@ -668,14 +676,16 @@ def main():
                        "N": N, "M": w.code.n_checks, "E": w.code.n_edges, "K": K,
                        "ebn0_db": w.ebn0_db, "rule": w.params["rule"], "early_stop": 0,
                        "l2": "flushed between timed steps (256 MB write)", "frames_per_rank": F,
-                       "kernel": args.kernel},
+                       "kernel": args.kernel, "schedule": args.schedule},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(host_llr.nbytes),
                     "d2h_bytes_per_step": int(bits.numel() + iters.numel() * 4 + ok.numel())},
-            "gpu_launches": args.steps * (1 if ws_bytes == 0 else 3 + 2 * w.params["max_iter"]),
+            "gpu_launches": args.steps * (1 if (ws_bytes == 0 or args.schedule == "layered")
+                                          else 3 + 2 * w.params["max_iter"]),
             "roofline": roofline, "clocks": clocks}
     if not args.no_cpu_baseline and args.dtype == "int8":
+        lay = ldpc.ldpc_code_layers(code.handle, w.code.n_checks)[1] if args.schedule == "layered" else None
         info, _ = cpu_oracle_sample(w, args.form, budget_s=float(os.environ.get("BENCH_CPU_BUDGET_S", "12")),
-                                    max_frames=F)
+                                    max_frames=F, layers=lay)
         line["cpu_baseline"] = info
     print(json.dumps(line), flush=True)
     return 0

@@ -94,6 +94,17 @@ enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2 };
  *                                         of ONCHIP_HALF with its conditions; for
  *                                         int8 single-scan codes too large for
  *                                         one SM; no workspace
+ *   schedule   LDPC_SCHEDULE_FLOODING (0): every check of an iteration reads the
+ *              posteriors of the previous iteration (Sections III-V).
+ *              LDPC_SCHEDULE_LAYERED (1): the single scan of Eq. (3) in a layered
+ *              schedule (layered decoding is cited in Section I; the paper's own
+ *              schedule is flooding): the checks are grouped into layers whose
+ *              checks share no variable (ldpc_code_layers); within an iteration
+ *              the layers run in order and each check updates its variables'
+ *              posteriors in place, Z_n <- Z_n - L^(k-1)_mn + L^(k)_mn.  The stop
+ *              rule is checked after whole iterations.  int8, SS_FIXED or
+ *              SS_1BIT, kernel AUTO, the binary16 conditions of ONCHIP_HALF
+ *              (N unrestricted); needs a workspace.
  */
 typedef struct {
   int32_t dtype;
@@ -108,7 +119,10 @@ typedef struct {
   int32_t max_iter;
   int32_t early_stop;
   int32_t kernel;
+  int32_t schedule;
 } ldpc_decode_params;
+
+enum { LDPC_SCHEDULE_FLOODING = 0, LDPC_SCHEDULE_LAYERED = 1 };
 
 enum {
   LDPC_KERNEL_AUTO = 0,
@@ -173,6 +187,18 @@ LDPC_API ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_
 /* Degree classes of a code: the distinct check degrees in ascending order.
  * degrees (host, nullable) receives n_classes entries (at most 31). */
 LDPC_API ldpc_status ldpc_code_degree_classes(const ldpc_code *code, int32_t *n_classes, int32_t *degrees);
+
+/* Layers of the layered schedule: *n_layers and, in layer_of_check (host,
+ * nullable, n_checks entries), the layer of every check.  The default partition
+ * (built by ldpc_code_create) takes the checks in row order and puts each into
+ * the lowest layer none of whose checks shares a variable with it. */
+LDPC_API ldpc_status ldpc_code_layers(const ldpc_code *code, int32_t *n_layers, int32_t *layer_of_check);
+
+/* Replaces the layer partition (for instance the block rows of a
+ * quasi-cyclic code).  layer_of_check: host, n_checks entries in [0, n_layers);
+ * the checks of one layer must share no variable (else LDPC_ERR_INVALID_ARG and
+ * the old partition stays).  Synchronises the code's device first. */
+LDPC_API ldpc_status ldpc_code_set_layers(ldpc_code *code, int32_t n_layers, const int32_t *layer_of_check);
 
 /* Bytes of device workspace that ldpc_learned_forward / _loss / _backward share
  * for n_iters iterations and n_frames frames: per-iteration checkpoints of the
@@ -289,8 +315,9 @@ LDPC_API ldpc_status ldpc_decode_batch_noalloc(const ldpc_code *code, const ldpc
 /* One code of a batch.
  *   code        a code created on the batch's device.
  *   params      dtype LDPC_DTYPE_INT8, form SS_FIXED or SS_1BIT (the same form
- *               for every job of a batch), any rule; kernel is ignored.  The
- *               code must meet the binary16 conditions of LDPC_KERNEL_ONCHIP_HALF.
+ *               for every job of a batch), any rule, flooding schedule; kernel
+ *               is ignored.  The code must meet the binary16 conditions of
+ *               LDPC_KERNEL_ONCHIP_HALF.
  *   llr, n_frames and the outputs: device buffers as in ldpc_decode_batch
  *   (llr_out may be NULL).  n_frames == 0 drops the job. */
 typedef struct {

@@ -2,6 +2,7 @@
 // a code, error reporting and the device guard.  Not part of the public ABI.
 #pragma once
 #include <string>
+#include <vector>
 
 #include "../../include/ldpc_gb300.h"
 #include "kernels.h"
@@ -43,6 +44,14 @@ struct ldpc_code {
   int sm_count = 0;
   size_t smem_optin = 0;
   ClusterTables ctab[kClusterSizes];
+  // layered schedule: layer of every check (original order) and, on the device,
+  // the internal check indices of each layer
+  std::vector<int32_t> layer_of_check;
+  int32_t n_layers = 0;
+  int32_t* d_lay_ptr = nullptr;   // [n_layers + 1]
+  int32_t* d_lay_rows = nullptr;  // [M]
+  std::vector<int32_t> pos;       // internal index of each original check
+  std::vector<int32_t> h_row_ptr, h_col_idx;
 };
 
 namespace ldpc_api {
@@ -66,6 +75,8 @@ struct DeviceGuard {
 };
 
 ldpc::DevCode view(const ldpc_code* c);
+// Uploads a layer partition (validated: the checks of a layer share no variable).
+ldpc_status set_layers(ldpc_code* c, int32_t n_layers, const int32_t* layer_of_check);
 ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p);
 
 // Cluster split of a code (multi_api.cu): built by ldpc_code_create for every

@@ -121,9 +121,12 @@ __device__ __forceinline__ uint32_t row_parity_body(const Addr& ad, const uint16
 //       31 - j, so that shifting the word left by j (a running S + S) brings both
 //       to the binary16 sign bits}
 //   Lm  (FORM 0) [ell_w][rows][P] u16: L + 128 per frame (one byte each)
-//   DELTA: add L^(k) - L^(k-1) instead of L^(k) (an accumulator that holds
-//       Z^(k-1) and is never reset; used by the streaming kernels)
-template <int G, int FORM, int D, int DMAX, bool ES, class Addr, bool DELTA = false>
+//   ACC: how the new messages reach the posteriors.  0: add L^(k) into the
+//       accumulator; 1: add L^(k) - L^(k-1) (an accumulator that holds Z^(k-1)
+//       and is never reset; the streaming kernels); 2: update the posterior in
+//       place, Z_n <- Z_n + L^(k) - L^(k-1), through Addr::update (the layered
+//       schedule, where the checks running together share no variable)
+template <int G, int FORM, int D, int DMAX, bool ES, class Addr, int ACC = 0>
 __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* __restrict__ tab,
                                                const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
                                                const H2Rule& rule, uint32_t qm2, int m, int d,
@@ -132,7 +135,7 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
   constexpr int NJ = D > 0 ? D : DMAX;
   // one frame pair: the pass-1 handles stay in registers for pass 2; two pairs
   // need those registers for state and reload them
-  constexpr bool KEEP = (P == 1 && FORM == 1 && !ES);
+  constexpr bool KEEP = (P == 1 && FORM == 1 && !ES && ACC != 2);
   using H = typename Addr::H;
   uint32_t A2[P], B2[P], I2[P], S[P];
   if constexpr (FORM == 1) {
@@ -219,7 +222,7 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
   for (int p = 0; p < P; ++p) {
     SN[p] = Sn[p];
     Dn[p] = hsub(Bn[p], An[p]);
-    if constexpr (DELTA && FORM == 1) SO[p] = S[p];
+    if constexpr (ACC != 0 && FORM == 1) SO[p] = S[p];
   }
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
@@ -229,7 +232,7 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
       else n = ad.at(tab, Zs, j, m);
       uint32_t sv = 0;
       uint32_t lold = 0;
-      if constexpr (DELTA && FORM == 0) {
+      if constexpr (ACC != 0 && FORM == 0) {
         if constexpr (P == 1) lold = Lm[ad.lm(j, m)];
         else lold = reinterpret_cast<const uint32_t*>(Lm)[ad.lm(j, m)];
       }
@@ -238,9 +241,9 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
         const uint32_t L = hfma(Dn[p], heq_one(In[p], h2c(j)), An[p]) ^ (SN[p] & 0x80008000u);
         SN[p] += SN[p];
         int32_t v = (int32_t)hadd(L, h2c(1536));
-        if constexpr (DELTA) {
+        uint32_t Lo = 0;
+        if constexpr (ACC != 0) {
           // the previous message of this position, as in pass 1
-          uint32_t Lo;
           if constexpr (FORM == 1) {
             Lo = hfma(D2[p], heq_one(I2[p], h2c(j)), A2[p]) ^ (SO[p] & 0x80008000u);
             SO[p] += SO[p];
@@ -252,7 +255,8 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
           // (L - Lo)_lo + 65536 (L - Lo)_hi
           v -= (int32_t)hadd(Lo, h2c(1536));
         }
-        ad.add(Acc, n, p, v);
+        if constexpr (ACC == 2) ad.update(n, p, L, Lo);
+        else ad.add(Acc, n, p, v);
         if constexpr (FORM == 0) {
           const uint32_t hb = hfma(L, 0x30003000u /* 0.125 */, h2c(144));
           sv |= (uint32_t)__byte_perm(hb, 0u, 0x4420) << (16 * p);

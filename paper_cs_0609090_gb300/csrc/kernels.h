@@ -89,6 +89,19 @@ size_t multi_local_slot_bytes(int N, int M, int ell_w, int form, size_t* acc_off
 cudaError_t multi_launch(int form, bool es, const MultiParams& mp, int threads, size_t smem, int grid,
                          cudaStream_t st, int* max_grid);
 
+// The single scan in a layered schedule (layered_h2.cu): frame-pair chunks,
+// one CTA per chunk, state in the workspace.  lay_ptr [n_layers + 1] and
+// lay_rows [M]: the internal check indices of each layer.
+struct LayeredLayout {
+  int chunks = 0;
+  size_t st_off = 0, chunk_bytes = 0, total = 0;
+};
+LayeredLayout layered_layout(int form, int N, int M, int ell_w, int F);
+cudaError_t layered_decode(const DevCode& c, const IntRule& r, int form, const int32_t* lay_ptr,
+                           const int32_t* lay_rows, int n_layers, const int8_t* llr, int32_t F, int32_t max_iter,
+                           int32_t early_stop, uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout, void* ws,
+                           const LayeredLayout& L, int sm_count, size_t smem_optin, cudaStream_t st);
+
 // Device-memory (streaming) decoders for codes whose frame state does not fit
 // one SM.  All state lives in the caller's workspace (layout below).
 struct StreamLayout {

@@ -57,6 +57,61 @@ ldpc::DevCode view(const ldpc_code* c) {
   return v;
 }
 
+ldpc_status set_layers(ldpc_code* c, int32_t n_layers, const int32_t* layer_of_check) {
+  const int32_t M = c->M, N = c->N;
+  if (n_layers < 1 || n_layers > M || layer_of_check == nullptr)
+    return fail(LDPC_ERR_INVALID_ARG, "n_layers %d outside [1, %d] or layer_of_check NULL", n_layers, M);
+  std::vector<int32_t> owner((size_t)N, -1), count((size_t)n_layers + 1, 0);
+  std::vector<int32_t> seen_layer((size_t)N, -1);
+  for (int32_t m = 0; m < M; ++m) {
+    const int32_t l = layer_of_check[m];
+    if (l < 0 || l >= n_layers) return fail(LDPC_ERR_INVALID_ARG, "check %d in layer %d of %d", m, l, n_layers);
+    count[(size_t)l + 1]++;
+  }
+  // the checks of one layer must share no variable
+  std::vector<int32_t> by_layer((size_t)M);
+  std::vector<int32_t> fill(count.begin(), count.end() - 1);
+  for (int32_t l = 0; l < n_layers; ++l) count[(size_t)l + 1] += count[(size_t)l];
+  for (int32_t l = 0; l < n_layers; ++l) fill[(size_t)l] = count[(size_t)l];
+  for (int32_t m = 0; m < M; ++m) by_layer[(size_t)fill[(size_t)layer_of_check[m]]++] = m;
+  for (int32_t l = 0; l < n_layers; ++l)
+    for (int32_t i = count[(size_t)l]; i < count[(size_t)l + 1]; ++i) {
+      const int32_t m = by_layer[(size_t)i];
+      for (int32_t e = c->h_row_ptr[(size_t)m]; e < c->h_row_ptr[(size_t)m + 1]; ++e) {
+        const int32_t n = c->h_col_idx[(size_t)e];
+        if (seen_layer[(size_t)n] == l)
+          return fail(LDPC_ERR_INVALID_ARG, "layer %d: checks %d and %d share variable %d", l, owner[(size_t)n], m, n);
+        seen_layer[(size_t)n] = l;
+        owner[(size_t)n] = m;
+      }
+    }
+  // device lists: the internal (degree-sorted) index of every check, per layer
+  std::vector<int32_t> rows((size_t)M);
+  for (int32_t l = 0; l < n_layers; ++l) {
+    for (int32_t i = count[(size_t)l]; i < count[(size_t)l + 1]; ++i)
+      rows[(size_t)i] = c->pos[(size_t)by_layer[(size_t)i]];
+    std::sort(rows.begin() + count[(size_t)l], rows.begin() + count[(size_t)l + 1]);
+  }
+  int32_t *dp = nullptr, *dr = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&dp, sizeof(int32_t) * ((size_t)n_layers + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&dr, sizeof(int32_t) * (size_t)M)) != cudaSuccess ||
+      (e = cudaMemcpy(dp, count.data(), sizeof(int32_t) * ((size_t)n_layers + 1), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(dr, rows.data(), sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(dp);
+    cudaFree(dr);
+    return cuda_fail(e, "layer tables");
+  }
+  cudaFree(c->d_lay_ptr);
+  cudaFree(c->d_lay_rows);
+  c->d_lay_ptr = dp;
+  c->d_lay_rows = dr;
+  c->n_layers = n_layers;
+  c->layer_of_check.assign(layer_of_check, layer_of_check + M);
+  return LDPC_OK;
+}
+
 ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   if (p->dtype != LDPC_DTYPE_INT8 && p->dtype != LDPC_DTYPE_F32)
     return fail(LDPC_ERR_INVALID_ARG, "dtype %d is not LDPC_DTYPE_INT8/F32", p->dtype);
@@ -69,6 +124,8 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
     return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");
   if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_CLUSTER)
     return fail(LDPC_ERR_INVALID_ARG, "kernel %d is not a known LDPC_KERNEL_*", p->kernel);
+  if (p->schedule != LDPC_SCHEDULE_FLOODING && p->schedule != LDPC_SCHEDULE_LAYERED)
+    return fail(LDPC_ERR_INVALID_ARG, "schedule %d is not a known LDPC_SCHEDULE_*", p->schedule);
   if (p->dtype == LDPC_DTYPE_INT8) {
     if (p->msg_sat < 1 || p->msg_sat > 127)
       return fail(LDPC_ERR_INVALID_ARG, "msg_sat %d outside [1, 127]", p->msg_sat);
@@ -100,14 +157,28 @@ namespace {
 
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
-  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, STREAM_F32, ONCHIP_TWOSCAN } kind = NONE;
+  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, STREAM_F32, ONCHIP_TWOSCAN, LAYERED } kind = NONE;
   ldpc::OnchipPlan onchip;
   ldpc::StreamLayout stream;
+  ldpc::LayeredLayout layered;
   size_t ws = 0;
 };
 
 ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_frames, Choice* ch) {
   const ldpc::DevCode v = view(c);
+  if (p->schedule == LDPC_SCHEDULE_LAYERED) {
+    if (p->dtype != LDPC_DTYPE_INT8 || p->form == LDPC_FORM_TWO_SCAN || p->kernel != LDPC_KERNEL_AUTO)
+      return fail(LDPC_ERR_UNSUPPORTED, "the layered schedule runs int8 single-scan decodes (SS_FIXED or SS_1BIT) "
+                  "with kernel = LDPC_KERNEL_AUTO");
+    if (!ldpc::onchip_h2_eligible(65535, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num))
+      return fail(LDPC_ERR_UNSUPPORTED, "the layered schedule needs row degree <= 16 and "
+                  "128 + (max_col_degree + 1) * msg_sat <= 2048");
+    const int form = p->form == LDPC_FORM_SS_1BIT ? 1 : 0;
+    ch->kind = Choice::LAYERED;
+    ch->layered = ldpc::layered_layout(form, c->N, c->M, c->ell_w, n_frames);
+    ch->ws = ch->layered.total;
+    return LDPC_OK;
+  }
   if (p->dtype == LDPC_DTYPE_INT8 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED)) {
     const int form = p->form == LDPC_FORM_SS_1BIT ? 1 : 0;
     const bool want_half = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF;
@@ -318,6 +389,31 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
     ldpc_code_destroy(c);
     return cs;
   }
+  // default layers for the layered schedule: checks in row order, each into the
+  // lowest layer none of whose checks shares a variable with it
+  c->pos = pos;
+  c->h_row_ptr.assign(row_ptr, row_ptr + n_checks + 1);
+  c->h_col_idx.assign(col_idx, col_idx + E);
+  {
+    std::vector<int32_t> layer((size_t)n_checks, 0);
+    std::vector<std::vector<uint8_t>> used;
+    for (int32_t m = 0; m < n_checks; ++m) {
+      size_t l = 0;
+      for (; l < used.size(); ++l) {
+        bool free_here = true;
+        for (int32_t e = row_ptr[m]; e < row_ptr[m + 1] && free_here; ++e) free_here = !used[l][(size_t)col_idx[e]];
+        if (free_here) break;
+      }
+      if (l == used.size()) used.emplace_back((size_t)n_vars, (uint8_t)0);
+      for (int32_t e = row_ptr[m]; e < row_ptr[m + 1]; ++e) used[l][(size_t)col_idx[e]] = 1;
+      layer[(size_t)m] = (int32_t)l;
+    }
+    const ldpc_status ls = set_layers(c, (int32_t)used.size(), layer.data());
+    if (ls != LDPC_OK) {
+      ldpc_code_destroy(c);
+      return ls;
+    }
+  }
   *out = c;
   return LDPC_OK;
 }
@@ -336,6 +432,8 @@ ldpc_status ldpc_code_destroy(ldpc_code* code) {
   cudaFree(code->d_cptr);
   cudaFree(code->d_cslot);
   cudaFree(code->d_rclass);
+  cudaFree(code->d_lay_ptr);
+  cudaFree(code->d_lay_rows);
   free_cluster_tables(code);
   delete code;
   return LDPC_OK;
@@ -409,6 +507,11 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
     err = ldpc::onchip_h2_launch(v, r, form, ch.onchip, code->sm_count, static_cast<const int8_t*>(llr), n_frames,
                                  params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
                                  static_cast<int16_t*>(llr_out), st, false);
+  } else if (ch.kind == Choice::LAYERED) {
+    err = ldpc::layered_decode(v, r, form, code->d_lay_ptr, code->d_lay_rows, code->n_layers,
+                               static_cast<const int8_t*>(llr), n_frames, params->max_iter, params->early_stop,
+                               hard_bits, iters_used, syndrome_ok, static_cast<int16_t*>(llr_out), workspace,
+                               ch.layered, code->sm_count, code->smem_optin, st);
   } else if (ch.kind == Choice::CLUSTER_H2) {
     err = cluster_decode(code, params, static_cast<const int8_t*>(llr), n_frames, hard_bits, iters_used, syndrome_ok,
                          static_cast<int16_t*>(llr_out), st);
@@ -442,6 +545,23 @@ ldpc_status ldpc_code_degree_classes(const ldpc_code* code, int32_t* n_classes, 
   if (degrees != nullptr)
     for (int32_t q = 0; q < code->n_classes; ++q) degrees[q] = code->class_deg[q];
   return LDPC_OK;
+}
+
+ldpc_status ldpc_code_layers(const ldpc_code* code, int32_t* n_layers, int32_t* layer_of_check) {
+  g_last_error.clear();
+  if (code == nullptr || n_layers == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code and n_layers must be non-NULL");
+  *n_layers = code->n_layers;
+  if (layer_of_check != nullptr)
+    std::copy(code->layer_of_check.begin(), code->layer_of_check.end(), layer_of_check);
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_code_set_layers(ldpc_code* code, int32_t n_layers, const int32_t* layer_of_check) {
+  g_last_error.clear();
+  if (code == nullptr) return fail(LDPC_ERR_INVALID_ARG, "code is NULL");
+  DeviceGuard guard(code->device);
+  cudaDeviceSynchronize();  // no decode in flight may read the old tables
+  return set_layers(code, n_layers, layer_of_check);
 }
 
 namespace {
@@ -590,8 +710,10 @@ ldpc_status ldpc_decode_batch_noalloc(const ldpc_code* code, const ldpc_decode_p
   ldpc_status s = check_params(code, params);
   if (s != LDPC_OK) return s;
   if (params->dtype != LDPC_DTYPE_INT8 || params->form == LDPC_FORM_TWO_SCAN ||
-      (params->kernel != LDPC_KERNEL_AUTO && params->kernel != LDPC_KERNEL_STREAM))
-    return fail(LDPC_ERR_UNSUPPORTED, "the no-allocation entry point runs the int8 single-scan streaming decoder only");
+      (params->kernel != LDPC_KERNEL_AUTO && params->kernel != LDPC_KERNEL_STREAM) ||
+      params->schedule != LDPC_SCHEDULE_FLOODING)
+    return fail(LDPC_ERR_UNSUPPORTED, "the no-allocation entry point runs the int8 single-scan streaming decoder "
+                "(flooding schedule) only");
   if (!ldpc::stream_int8_eligible(code->max_row_deg, code->max_col_deg, params->msg_sat))
     return fail(LDPC_ERR_UNSUPPORTED, "code degrees / msg_sat are outside the streaming int8 decoder's range");
   if (n_frames == 0) return LDPC_OK;

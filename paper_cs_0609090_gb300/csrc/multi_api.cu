@@ -425,8 +425,10 @@ ldpc_status ldpc_multi_create(ldpc_multi** out, const ldpc_multi_job* jobs, int3
     else if (jb.n_frames < 0) s = fail(LDPC_ERR_INVALID_ARG, "job %d: n_frames %d < 0", j, jb.n_frames);
     else if ((s = check_params(jb.code, &jb.params)) != LDPC_OK) fail(s, "job %d: %s", j, ldpc_last_error());
     else if (jb.params.dtype != LDPC_DTYPE_INT8 ||
-             (jb.params.form != LDPC_FORM_SS_FIXED && jb.params.form != LDPC_FORM_SS_1BIT))
-      s = fail(LDPC_ERR_UNSUPPORTED, "job %d: batches run int8 single-scan decodes (SS_FIXED or SS_1BIT)", j);
+             (jb.params.form != LDPC_FORM_SS_FIXED && jb.params.form != LDPC_FORM_SS_1BIT) ||
+             jb.params.schedule != LDPC_SCHEDULE_FLOODING)
+      s = fail(LDPC_ERR_UNSUPPORTED, "job %d: batches run int8 single-scan decodes (SS_FIXED or SS_1BIT, flooding "
+               "schedule)", j);
     else if (form >= 0 && jb.params.form != form)
       s = fail(LDPC_ERR_INVALID_ARG, "job %d: every job of a batch must use the same form", j);
     else if (device >= 0 && jb.code->device != device)

@@ -260,11 +260,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
     const int d = c.deg(m);
     using A = StreamAddr<WIDE>;
     switch (d) {
-      case 6: fail |= check_body<2, FORM, 6, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 7: fail |= check_body<2, FORM, 7, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 14: fail |= check_body<2, FORM, 14, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 15: fail |= check_body<2, FORM, 15, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      default: fail |= check_body<2, FORM, 0, 16, ES, A, DELTA>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 6: fail |= check_body<2, FORM, 6, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 7: fail |= check_body<2, FORM, 7, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 14: fail |= check_body<2, FORM, 14, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      case 15: fail |= check_body<2, FORM, 15, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      default: fail |= check_body<2, FORM, 0, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
     }
   }
   if (ES && fail) atomicOr(s.fail + cur * s.FP + p, fail);

@@ -28,6 +28,8 @@ DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_
 FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
 RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED}
 LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM, LDPC_KERNEL_CLUSTER = range(5)
+LDPC_SCHEDULE_FLOODING, LDPC_SCHEDULE_LAYERED = 0, 1
+SCHEDULES = {"flooding": LDPC_SCHEDULE_FLOODING, "layered": LDPC_SCHEDULE_LAYERED}
 KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF,
            "stream": LDPC_KERNEL_STREAM, "cluster": LDPC_KERNEL_CLUSTER}
 
@@ -37,7 +39,7 @@ EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_work
            "ldpc_learned_workspace_size", "ldpc_learned_forward", "ldpc_learned_loss", "ldpc_learned_backward",
            "ldpc_adam_step", "ldpc_awgn_llr_f32", "ldpc_quantize_llr", "ldpc_multi_create", "ldpc_multi_destroy",
            "ldpc_multi_workspace_size", "ldpc_multi_decode", "ldpc_multi_autotune", "ldpc_multi_info",
-           "ldpc_last_error")
+           "ldpc_code_layers", "ldpc_code_set_layers", "ldpc_last_error")
 NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -52,7 +54,7 @@ class ldpc_decode_params(ctypes.Structure):
                 ("offset", ctypes.c_int32), ("norm_num", ctypes.c_int32), ("norm_shift", ctypes.c_int32),
                 ("offset_f32", ctypes.c_float), ("norm_f32", ctypes.c_float),
                 ("msg_sat", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("early_stop", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+                ("early_stop", ctypes.c_int32), ("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
 class ldpc_multi_job(ctypes.Structure):
@@ -87,6 +89,8 @@ _lib.ldpc_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, 
 _lib.ldpc_awgn_llr_f32.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]
 _lib.ldpc_quantize_llr.argtypes = [_P, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, _P, _P]
+_lib.ldpc_code_layers.argtypes = [_P, _P, _P]
+_lib.ldpc_code_set_layers.argtypes = [_P, ctypes.c_int32, _P]
 _lib.ldpc_multi_create.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(ldpc_multi_job), ctypes.c_int32,
                                    ctypes.POINTER(ldpc_multi_tuning)]
 _lib.ldpc_multi_destroy.argtypes = [_P]
@@ -128,9 +132,9 @@ def ldpc_last_error() -> str:
 
 def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=3, norm_shift=2,
                 offset_f32=0.0, norm_f32=0.75, msg_sat=127, max_iter=20, early_stop=1,
-                norm=None, kernel="auto", **_ignored) -> ldpc_decode_params:
+                norm=None, kernel="auto", schedule="flooding", **_ignored) -> ldpc_decode_params:
     """Builds ldpc_decode_params from names ('int8'/'f32', 'ss_fixed'/'ss_1bit'/'two_scan',
-    'plain'/'offset'/'normalized').  ``norm`` is an alias for norm_f32."""
+    'plain'/'offset'/'normalized', 'flooding'/'layered').  ``norm`` is an alias for norm_f32."""
     if norm is not None:
         norm_f32 = norm
     return ldpc_decode_params(DTYPES[dtype] if isinstance(dtype, str) else dtype,
@@ -138,7 +142,8 @@ def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=
                               RULES[rule] if isinstance(rule, str) else rule,
                               int(offset), int(norm_num), int(norm_shift), float(offset_f32),
                               float(norm_f32), int(msg_sat), int(max_iter), int(early_stop),
-                              KERNELS[kernel] if isinstance(kernel, str) else int(kernel))
+                              KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
+                              SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule))
 
 
 def ldpc_code_create(n_vars: int, n_checks: int, row_ptr, col_idx, device: int = 0) -> int:
@@ -238,6 +243,19 @@ def ldpc_awgn_llr_f32(n_vars: int, seed: int, first_frame: int, n_frames: int, e
 def ldpc_quantize_llr(llr, n: int, delta: float, qc: int, q, stream=None) -> None:
     _check(_lib.ldpc_quantize_llr(_ptr(llr), int(n), float(delta), int(qc), _ptr(q), _stream_handle(stream)),
            "ldpc_quantize_llr")
+
+
+def ldpc_code_layers(code: int, n_checks: int):
+    """(n_layers, layer_of_check int32 [n_checks]) of the layered schedule."""
+    n = ctypes.c_int32()
+    lay = np.zeros(n_checks, np.int32)
+    _check(_lib.ldpc_code_layers(_P(code), ctypes.byref(n), _ptr(lay)), "ldpc_code_layers")
+    return n.value, lay
+
+
+def ldpc_code_set_layers(code: int, layer_of_check) -> None:
+    lay = np.ascontiguousarray(layer_of_check, dtype=np.int32)
+    _check(_lib.ldpc_code_set_layers(_P(code), int(lay.max()) + 1, _ptr(lay)), "ldpc_code_set_layers")
 
 
 def ldpc_multi_create(jobs, tuning: ldpc_multi_tuning | None = None) -> int:

@@ -34,10 +34,29 @@ def test_library_exports_every_declared_symbol(L):
     assert declared == set(L.EXPORTS)
 
 
-def test_params_struct_layout(L):
-    # 12 four-byte fields, as in ldpc_decode_params
-    assert ctypes.sizeof(L.ldpc_decode_params) == 48
-    assert [f[0] for f in L.ldpc_decode_params._fields_][-1] == "kernel"
+def test_struct_layouts_match_the_header(L, tmp_path):
+    """sizeof and offsetof of every field of the ABI structs, compiled from the
+    header with gcc, equal the binding's ctypes definitions."""
+    import subprocess
+    structs = {"ldpc_decode_params": L.ldpc_decode_params, "ldpc_multi_job": L.ldpc_multi_job,
+               "ldpc_multi_tuning": L.ldpc_multi_tuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ldpc_gb300.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(__file__), "..", "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(out[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
 
 
 def _create_raw(L, n_vars, n_checks, rp, ci):
