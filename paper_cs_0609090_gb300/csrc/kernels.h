@@ -93,14 +93,18 @@ cudaError_t multi_launch(int form, bool es, const MultiParams& mp, int threads, 
 // one CTA per chunk, state in the workspace.  lay_ptr [n_layers + 1] and
 // lay_rows [M]: the internal check indices of each layer.
 struct LayeredLayout {
-  int chunks = 0;
+  int chunks = 0, pw = 8;     // frame pairs per chunk (one CTA each)
+  bool sidx = false;          // column table in shared memory
+  bool zsm = false;           // the chunk's posteriors in shared memory
+  size_t smem = 0, zsm_off = 0;
+  size_t hdr = 0;             // workspace: queue counter, then per chunk [Z][state]
   size_t st_off = 0, chunk_bytes = 0, total = 0;
 };
-LayeredLayout layered_layout(int form, int N, int M, int ell_w, int F);
+LayeredLayout layered_layout(int form, int N, int M, int ell_w, int F, bool narrow, size_t smem_optin);
 cudaError_t layered_decode(const DevCode& c, const IntRule& r, int form, const int32_t* lay_ptr,
                            const int32_t* lay_rows, int n_layers, const int8_t* llr, int32_t F, int32_t max_iter,
                            int32_t early_stop, uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout, void* ws,
-                           const LayeredLayout& L, int sm_count, size_t smem_optin, cudaStream_t st);
+                           const LayeredLayout& L, int sm_count, cudaStream_t st);
 
 // Device-memory (streaming) decoders for codes whose frame state does not fit
 // one SM.  All state lives in the caller's workspace (layout below).

@@ -11,15 +11,18 @@
 // schedule is flooding.)  The stop rule checks the decisions after each whole
 // iteration (and before the first) with a parity pass over all checks.
 //
-// Frames are split into chunks of kPW frame pairs; one CTA owns a chunk for the
-// whole decode, so only its own barrier separates the layers.  Chunk state in
-// the caller's workspace, chunk-major with the pair innermost:
-//   Z  [N][kPW] half2                         posterior pairs
-//   St [M][kPW] uint4 (Section V state)  or  Lm [ell_w M][kPW] u16 (per edge)
-// A thread owns one check of the current layer for one pair (kThreads / kPW
+// Frames are split into chunks of PW frame pairs; one CTA owns a chunk for the
+// whole decode, so only its own barrier separates the layers.  Chunk state,
+// chunk-major with the pair innermost:
+//   Z  [N][PW] half2      posterior pairs: in shared memory when they fit next
+//                         to the column table (ZSM, PW = 4), else in the
+//                         workspace (PW = 8)
+//   St [M][PW] uint4 (Section V state)  or  Lm [ell_w M][PW] u16 (per edge), in
+//                         the workspace
+// A thread owns one check of the current layer for one pair (kThreads / PW
 // checks per step).  512 threads: the in-place body needs about 128 registers
-// (measured on the N=7493 code, 30 iterations: 5.38 ms against 5.80 ms with
-// 1024 threads limited to 64 registers and spilling).
+// (measured on the N=7493 code, 30 iterations, Z in the workspace: 5.38 ms
+// against 5.80 ms with 1024 threads limited to 64 registers and spilling).
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -30,9 +33,7 @@
 namespace ldpc {
 namespace {
 
-constexpr int kPW = 8;
 constexpr int kThreads = 512;
-constexpr int kSlots = kThreads / kPW;  // checks of a layer per step
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -40,7 +41,7 @@ __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(2
 // base; the column index comes from the degree-sorted edge-slot table (shared
 // memory copy when SIDX).  sel: the halves this lane may change (frames still
 // running).
-template <bool WIDE, bool SIDX>
+template <bool WIDE, bool SIDX, int kPW>
 struct LayAddr {
   using H = uint32_t;
   int M;
@@ -82,17 +83,18 @@ __device__ __forceinline__ int32_t q0v(const int8_t* __restrict__ llr, int32_t N
   return f < F ? (int32_t)__ldg(llr + (size_t)f * N + n) : 0;
 }
 
-template <int FORM, bool ES, bool WIDE, bool SIDX>
+template <int FORM, bool ES, bool WIDE, bool SIDX, int kPW, bool ZSM>
 __global__ void __launch_bounds__(kThreads, 1)
 layered_kernel(const DevCode c, const IntRule r, const int32_t* __restrict__ lay_ptr,
                const int32_t* __restrict__ lay_rows, int32_t n_layers, const int8_t* __restrict__ llr, int32_t F,
                int32_t max_iter, uint8_t* __restrict__ bits, int32_t* __restrict__ iters,
                uint8_t* __restrict__ okf, int16_t* __restrict__ zout, void* ws, size_t chunk_bytes,
-               size_t st_off, int32_t n_chunks) {
+               size_t st_off, int32_t n_chunks, uint32_t zsm_off, int32_t* __restrict__ queue) {
+  constexpr int kSlots = kThreads / kPW;  // checks of a layer per step
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_act[kPW], s_fail[kPW], s_ok[kPW];
   __shared__ int32_t s_iters[2 * kPW];
-  __shared__ int s_any;
+  __shared__ int s_any, s_chunk;
   const int tid = threadIdx.x;
   const int N = c.N, M = c.M;
   const int slot = tid / kPW, p = tid % kPW;
@@ -105,9 +107,15 @@ layered_kernel(const DevCode c, const IntRule r, const int32_t* __restrict__ lay
   const H2Rule hr = make_h2rule(r);
   const int N8 = (N + 7) >> 3;
 
-  for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+  // chunks from a queue in the workspace (frames that run to the cap make some
+  // chunks much longer than others under early stop)
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(queue, 1);
+    __syncthreads();
+    const int ch = s_chunk;
+    if (ch >= n_chunks) break;
     unsigned char* base = static_cast<unsigned char*>(ws) + (size_t)ch * chunk_bytes;
-    uint32_t* Z = reinterpret_cast<uint32_t*>(base);
+    uint32_t* Z = ZSM ? reinterpret_cast<uint32_t*>(smem + zsm_off) : reinterpret_cast<uint32_t*>(base);
     uint4* St = reinterpret_cast<uint4*>(base + st_off);
     uint16_t* Lm = reinterpret_cast<uint16_t*>(base + st_off);
     const int pair0 = ch * kPW;
@@ -131,7 +139,7 @@ layered_kernel(const DevCode c, const IntRule r, const int32_t* __restrict__ lay
       s_iters[2 * tid + 1] = max_iter;
     }
     __syncthreads();
-    LayAddr<WIDE, SIDX> ad{M, SIDX ? stab : c.ell16, c.ell32, Z + p, 0u};
+    LayAddr<WIDE, SIDX, kPW> ad{M, SIDX ? stab : c.ell16, c.ell32, Z + p, 0u};
 
     // parity of the decisions of every check, ORed per pair lane into s_fail
     auto syndrome = [&]() {
@@ -222,59 +230,74 @@ layered_kernel(const DevCode c, const IntRule r, const int32_t* __restrict__ lay
   }
 }
 
-template <int FORM, bool ES, bool WIDE, bool SIDX>
+template <int FORM, bool ES, bool WIDE, bool SIDX, int PW, bool ZSM>
 cudaError_t lay_launch_t(const DevCode& c, const IntRule& r, const int32_t* lay_ptr, const int32_t* lay_rows,
                          int n_layers, const int8_t* llr, int32_t F, int32_t max_iter, uint8_t* bits, int32_t* iters,
                          uint8_t* ok, int16_t* zout, void* ws, const LayeredLayout& L, int sm_count,
                          cudaStream_t st) {
-  auto kern = layered_kernel<FORM, ES, WIDE, SIDX>;
-  const size_t smem = SIDX ? (((size_t)c.ell_w * c.M * 2 + 15) & ~size_t(15)) : 0;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = layered_kernel<FORM, ES, WIDE, SIDX, PW, ZSM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L.smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int grid = std::min(L.chunks, per_sm * sm_count);
-  kern<<<grid, kThreads, smem, st>>>(c, r, lay_ptr, lay_rows, n_layers, llr, F, max_iter, bits, iters, ok, zout,
-                                     ws, L.chunk_bytes, L.st_off, L.chunks);
+  char* w = static_cast<char*>(ws);
+  e = cudaMemsetAsync(w, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, L.smem, st>>>(c, r, lay_ptr, lay_rows, n_layers, llr, F, max_iter, bits, iters, ok, zout,
+                                       w + L.hdr, L.chunk_bytes, L.st_off, L.chunks, (uint32_t)L.zsm_off,
+                                       reinterpret_cast<int32_t*>(w));
   return cudaGetLastError();
 }
 
 }  // namespace
 
-LayeredLayout layered_layout(int form, int N, int M, int ell_w, int F) {
+LayeredLayout layered_layout(int form, int N, int M, int ell_w, int F, bool narrow, size_t smem_optin) {
   LayeredLayout L;
-  L.chunks = ((F + 1) / 2 + kPW - 1) / kPW;
-  L.st_off = al256((size_t)N * kPW * 4);
-  L.chunk_bytes = al256(L.st_off + (form == 1 ? (size_t)M * kPW * 16 : (size_t)ell_w * M * kPW * 2));
-  L.total = (size_t)L.chunks * L.chunk_bytes;
+  const size_t reserve = 1024;  // static shared memory, rounded up
+  const size_t tab = ((size_t)ell_w * M * 2 + 15) & ~size_t(15);
+  L.sidx = narrow && tab + reserve <= smem_optin;
+  // posteriors of a 4-pair chunk in shared memory next to the table
+  L.zsm = L.sidx && tab + (size_t)N * 4 * 4 + reserve <= smem_optin;
+  L.pw = L.zsm ? 4 : 8;
+  L.zsm_off = tab;
+  L.smem = (L.sidx ? tab : 0) + (L.zsm ? (size_t)N * L.pw * 4 : 0);
+  L.chunks = ((F + 1) / 2 + L.pw - 1) / L.pw;
+  L.st_off = L.zsm ? 0 : al256((size_t)N * L.pw * 4);
+  L.chunk_bytes = al256(L.st_off + (form == 1 ? (size_t)M * L.pw * 16 : (size_t)ell_w * M * L.pw * 2));
+  L.hdr = 256;  // the chunk queue counter
+  L.total = L.hdr + (size_t)L.chunks * L.chunk_bytes;
   return L;
 }
 
 cudaError_t layered_decode(const DevCode& c, const IntRule& r, int form, const int32_t* lay_ptr,
                            const int32_t* lay_rows, int n_layers, const int8_t* llr, int32_t F, int32_t max_iter,
                            int32_t early_stop, uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout, void* ws,
-                           const LayeredLayout& L, int sm_count, size_t smem_optin, cudaStream_t st) {
+                           const LayeredLayout& L, int sm_count, cudaStream_t st) {
   const bool es = early_stop != 0;
   const bool wide = c.ell16 == nullptr;
-  const bool sidx = !wide && ((size_t)c.ell_w * c.M * 2 + 1024 <= smem_optin);
-#define LDPC_LAY(FF, EE, WW, SS) \
-  if (form == FF && es == EE && wide == WW && sidx == SS) \
-    return lay_launch_t<FF, EE, WW, SS>(c, r, lay_ptr, lay_rows, n_layers, llr, F, max_iter, bits, iters, ok, zout, \
-                                        ws, L, sm_count, st);
-  LDPC_LAY(1, true, false, true)
-  LDPC_LAY(1, false, false, true)
-  LDPC_LAY(0, true, false, true)
-  LDPC_LAY(0, false, false, true)
-  LDPC_LAY(1, true, false, false)
-  LDPC_LAY(1, false, false, false)
-  LDPC_LAY(0, true, false, false)
-  LDPC_LAY(0, false, false, false)
-  LDPC_LAY(1, true, true, false)
-  LDPC_LAY(1, false, true, false)
-  LDPC_LAY(0, true, true, false)
-  LDPC_LAY(0, false, true, false)
+#define LDPC_LAY(FF, EE, WW, SS, PP, ZZ)                                                                          \
+  if (form == FF && es == EE && wide == WW && L.sidx == SS && L.pw == PP && L.zsm == ZZ)                         \
+    return lay_launch_t<FF, EE, WW, SS, PP, ZZ>(c, r, lay_ptr, lay_rows, n_layers, llr, F, max_iter, bits, iters, \
+                                                ok, zout, ws, L, sm_count, st);
+  LDPC_LAY(1, true, false, true, 4, true)
+  LDPC_LAY(1, false, false, true, 4, true)
+  LDPC_LAY(0, true, false, true, 4, true)
+  LDPC_LAY(0, false, false, true, 4, true)
+  LDPC_LAY(1, true, false, true, 8, false)
+  LDPC_LAY(1, false, false, true, 8, false)
+  LDPC_LAY(0, true, false, true, 8, false)
+  LDPC_LAY(0, false, false, true, 8, false)
+  LDPC_LAY(1, true, false, false, 8, false)
+  LDPC_LAY(1, false, false, false, 8, false)
+  LDPC_LAY(0, true, false, false, 8, false)
+  LDPC_LAY(0, false, false, false, 8, false)
+  LDPC_LAY(1, true, true, false, 8, false)
+  LDPC_LAY(1, false, true, false, 8, false)
+  LDPC_LAY(0, true, true, false, 8, false)
+  LDPC_LAY(0, false, true, false, 8, false)
 #undef LDPC_LAY
   return cudaErrorInvalidValue;
 }

@@ -175,7 +175,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
                   "128 + (max_col_degree + 1) * msg_sat <= 2048");
     const int form = p->form == LDPC_FORM_SS_1BIT ? 1 : 0;
     ch->kind = Choice::LAYERED;
-    ch->layered = ldpc::layered_layout(form, c->N, c->M, c->ell_w, n_frames);
+    ch->layered = ldpc::layered_layout(form, c->N, c->M, c->ell_w, n_frames, c->d_ell16 != nullptr, c->smem_optin);
     ch->ws = ch->layered.total;
     return LDPC_OK;
   }
@@ -511,7 +511,7 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
     err = ldpc::layered_decode(v, r, form, code->d_lay_ptr, code->d_lay_rows, code->n_layers,
                                static_cast<const int8_t*>(llr), n_frames, params->max_iter, params->early_stop,
                                hard_bits, iters_used, syndrome_ok, static_cast<int16_t*>(llr_out), workspace,
-                               ch.layered, code->sm_count, code->smem_optin, st);
+                               ch.layered, code->sm_count, st);
   } else if (ch.kind == Choice::CLUSTER_H2) {
     err = cluster_decode(code, params, static_cast<const int8_t*>(llr), n_frames, hard_bits, iters_used, syndrome_ok,
                          static_cast<int16_t*>(llr_out), st);
