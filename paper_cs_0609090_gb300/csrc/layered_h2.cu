@@ -29,6 +29,7 @@
 
 #include "h2_body.cuh"
 #include "kernels.h"
+#include "launch_util.h"
 
 namespace ldpc {
 namespace {
@@ -236,7 +237,7 @@ cudaError_t lay_launch_t(const DevCode& c, const IntRule& r, const int32_t* lay_
                          uint8_t* ok, int16_t* zout, void* ws, const LayeredLayout& L, int sm_count,
                          cudaStream_t st) {
   auto kern = layered_kernel<FORM, ES, WIDE, SIDX, PW, ZSM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), L.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L.smem);

@@ -23,6 +23,7 @@
 //               take Z^(k) = Acc, and Acc is reset to Z^(0) (Eq. (3) first line).
 // After the cap a final syndrome pass gives the flags of frames still running.
 #include "kernels.h"
+#include "launch_util.h"
 
 namespace ldpc {
 namespace {
@@ -314,7 +315,7 @@ cudaError_t launch_t(const DevCode& c, const IntRule& r, const OnchipPlan& plan,
                      int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits, int32_t* iters,
                      uint8_t* ok, int16_t* zout, cudaStream_t stream) {
   auto kern = onchip_int8_kernel<G, FORM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), plan.smem);
   if (e != cudaSuccess) return e;
   kern<<<plan.grid, plan.threads, plan.smem, stream>>>(c, r, llr, F, max_iter, early_stop, bits, iters,
                                                       ok, zout, plan.n_groups);
@@ -324,7 +325,7 @@ cudaError_t launch_t(const DevCode& c, const IntRule& r, const OnchipPlan& plan,
 template <int G, int FORM>
 cudaError_t occupancy_t(OnchipPlan* plan, int sm_count) {
   auto kern = onchip_int8_kernel<G, FORM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), plan->smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, plan->threads, plan->smem);

@@ -23,6 +23,7 @@
 
 #include "h2ops.cuh"
 #include "kernels.h"
+#include "launch_util.h"
 
 namespace ldpc {
 namespace {
@@ -283,7 +284,7 @@ cudaError_t ts_launch_t(const DevCode& c, const IntRule& r, OnchipPlan& plan, in
                         int32_t F, int32_t max_iter, uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout,
                         cudaStream_t stream) {
   auto kern = onchip_twoscan_kernel<G, DMAX, ES>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(kern), plan.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, plan.threads, plan.smem);
