@@ -21,9 +21,10 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = [os.path.join(_HERE, "ldpc_oracle.c")]
 
 TWO_SCAN, SS_FIXED, SS_1BIT = 0, 1, 2
-PLAIN, OFFSET, NORMALIZED = 0, 1, 2
+PLAIN, OFFSET, NORMALIZED, SUM_PRODUCT = 0, 1, 2, 3
 FORMS = {"two_scan": TWO_SCAN, "ss_fixed": SS_FIXED, "ss_1bit": SS_1BIT}
-RULES = {"plain": PLAIN, "offset": OFFSET, "normalized": NORMALIZED}
+RULES = {"plain": PLAIN, "offset": OFFSET, "normalized": NORMALIZED, "sum_product": SUM_PRODUCT}
+SPA_SAT = 30.0  # |input| saturation of the sum-product check rule
 
 
 def build(force: bool = False) -> str:

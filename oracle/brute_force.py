@@ -49,3 +49,21 @@ def max_marginals(cw: np.ndarray, q0: np.ndarray) -> np.ndarray:
         z1 = corr[:, cw[:, n] == 1].max(axis=1) if np.any(cw[:, n] == 1) else np.full(corr.shape[0], -np.inf)
         out[:, n] = 0.5 * (z0 - z1)
     return out
+
+
+def app_llr(cw: np.ndarray, q0: np.ndarray) -> np.ndarray:
+    """Exact a-posteriori LLRs for channel LLRs q0 (uniform prior over the
+    codewords): ln sum over codewords with x_n = 0 of exp(corr/2) minus the same
+    over x_n = 1, corr = sum_i (1 - 2 c_i) q0_i (the sum-product decoder's target,
+    exact on cycle-free Tanner graphs)."""
+    corr = 0.5 * correlations(cw, np.asarray(q0, dtype=float))       # F x C
+    out = np.zeros((corr.shape[0], cw.shape[1]))
+    for n in range(cw.shape[1]):
+        a, b = corr[:, cw[:, n] == 0], corr[:, cw[:, n] == 1]
+        la = a.max(axis=1) + np.log(np.exp(a - a.max(axis=1, keepdims=True)).sum(axis=1))
+        if b.shape[1] == 0:
+            out[:, n] = np.inf
+            continue
+        lb = b.max(axis=1) + np.log(np.exp(b - b.max(axis=1, keepdims=True)).sum(axis=1))
+        out[:, n] = la - lb
+    return out

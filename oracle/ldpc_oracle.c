@@ -107,6 +107,26 @@ static double check_rule_d(const double *in, int32_t d, int32_t j) {
   return (double)s * mn;
 }
 
+/* Sum-product check rule (log domain; cited in Section I as the rule min-sum
+   approximates), for one position j: the product of the signs of the other
+   inputs times phi(sum over the other inputs of phi(|in|)), with
+   phi(x) = -ln tanh(x/2) = ln(1 + 2/(e^x - 1)) (phi(0) = inf, phi(inf) = 0) and
+   the magnitudes saturated to ORC_SPA_SAT before phi. */
+static double phi_d(double x) { return log1p(2.0 / expm1(x)); }
+
+static double check_rule_spa_d(const double *in, int32_t d, int32_t j) {
+  int s = 1;
+  double sum = 0.0;
+  for (int32_t t = 0; t < d; ++t) {
+    if (t == j) continue;
+    s *= sgn_d(in[t]);
+    double a = fabs(in[t]);
+    if (a > ORC_SPA_SAT) a = ORC_SPA_SAT;
+    sum += phi_d(a);
+  }
+  return s == 0 ? 0.0 : (double)s * phi_d(sum);
+}
+
 /* ------------------------------------------------------- integer, one frame */
 
 typedef struct {
@@ -313,7 +333,7 @@ static void decode_frame_f64(const orc_code *c, const orc_csc *t, const orc_dpar
           int32_t d = rp[m + 1] - rp[m];
           for (int32_t j = 0; j < d; ++j) w->u[j] = w->Zmn[rp[m] + j];
           for (int32_t j = 0; j < d; ++j) {
-            double l = check_rule_d(w->u, d, j);
+            double l = p->rule == ORC_SUM_PRODUCT ? check_rule_spa_d(w->u, d, j) : check_rule_d(w->u, d, j);
             L[rp[m] + j] = sgn_d(l) * modify_d(p, k, m, M, fabs(l));
           }
         }
@@ -334,7 +354,7 @@ static void decode_frame_f64(const orc_code *c, const orc_csc *t, const orc_dpar
           int32_t d = rp[m + 1] - rp[m];
           for (int32_t j = 0; j < d; ++j) w->u[j] = Zprev[ci[rp[m] + j]] - L[rp[m] + j];
           for (int32_t j = 0; j < d; ++j) {
-            double l = check_rule_d(w->u, d, j);
+            double l = p->rule == ORC_SUM_PRODUCT ? check_rule_spa_d(w->u, d, j) : check_rule_d(w->u, d, j);
             w->Lraw[j] = sgn_d(l) * modify_d(p, k, m, M, fabs(l));
           }
           for (int32_t j = 0; j < d; ++j) {
@@ -554,12 +574,14 @@ int orc_decode_layered_int(const orc_code *code, const orc_iparams *p, const int
 int orc_decode_f64(const orc_code *code, const orc_dparams *p, int32_t form, const double *q0,
                    int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok, double *z_out,
                    double *l_out, int32_t n_threads) {
+  if (p && p->rule == ORC_SUM_PRODUCT && form == ORC_SS_1BIT) return -1; /* messages are not (A, B) pairs */
   return orc_decode_f64_margin(code, p, form, q0, n_frames, bits, iters, ok, z_out, l_out, NULL, n_threads);
 }
 
 int orc_decode_f64_margin(const orc_code *code, const orc_dparams *p, int32_t form, const double *q0,
                           int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok, double *z_out,
                           double *l_out, double *margin_out, int32_t n_threads) {
+  if (p && p->rule == ORC_SUM_PRODUCT && form == ORC_SS_1BIT) return -1;
   if (validate(code, form) || !p || p->max_iter < 0 || n_frames < 0) return -1;
   if (n_frames == 0) return 0;
   if (!q0 || !bits || !iters || !ok || !z_out) return -1;

@@ -38,7 +38,11 @@ extern "C" {
 #endif
 
 enum { ORC_TWO_SCAN = 0, ORC_SS_FIXED = 1, ORC_SS_1BIT = 2 };
-enum { ORC_PLAIN = 0, ORC_OFFSET = 1, ORC_NORMALIZED = 2 };
+enum { ORC_PLAIN = 0, ORC_OFFSET = 1, ORC_NORMALIZED = 2, ORC_SUM_PRODUCT = 3 };
+/* ORC_SUM_PRODUCT (double decoders, two-scan and per-edge single scan): the
+   sum-product check rule L = prod sgn x phi(sum phi(|in|)) over the other
+   positions, phi(x) = -ln tanh(x/2), magnitudes saturated to ORC_SPA_SAT. */
+#define ORC_SPA_SAT 30.0
 
 typedef struct {
   int32_t n_vars, n_checks;
