@@ -58,13 +58,17 @@ typedef struct ldpc_code ldpc_code;
 
 enum { LDPC_DTYPE_INT8 = 0, LDPC_DTYPE_F32 = 1 };
 enum { LDPC_FORM_SS_FIXED = 0, LDPC_FORM_SS_1BIT = 1, LDPC_FORM_TWO_SCAN = 2 };
-enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2 };
+enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2, LDPC_RULE_SUM_PRODUCT = 3 };
 
 /* Decoder settings (Section III: lambda_k, beta_k constant over k; cap).
  *   dtype      LDPC_DTYPE_INT8: llr is int8, messages are integers saturated to
  *              msg_sat; LDPC_DTYPE_F32: llr is float32.
  *   form       which of the three algorithms above runs.
- *   rule       PLAIN; OFFSET: |L| <- max(|L| - beta, 0); NORMALIZED: |L| <- lambda |L|.
+ *   rule       PLAIN; OFFSET: |L| <- max(|L| - beta, 0); NORMALIZED: |L| <- lambda |L|;
+ *              SUM_PRODUCT: the log-domain sum-product check rule that min-sum
+ *              approximates (Section I), as an accuracy reference: L_mn = prod of
+ *              the other inputs' signs x phi(sum over them of phi(min(|u|, 30))),
+ *              phi(x) = -ln tanh(x/2); float32 path, SS_FIXED form, flooding only.
  *   offset     int8 path: beta in LSBs (>= 0).
  *   norm_num,  int8 path: lambda = norm_num / 2^norm_shift, magnitude floored
  *   norm_shift (0 < norm_num <= 2^norm_shift, 0 <= norm_shift <= 8).

@@ -117,8 +117,11 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
     return fail(LDPC_ERR_INVALID_ARG, "dtype %d is not LDPC_DTYPE_INT8/F32", p->dtype);
   if (p->form < LDPC_FORM_SS_FIXED || p->form > LDPC_FORM_TWO_SCAN)
     return fail(LDPC_ERR_INVALID_ARG, "form %d is not a known LDPC_FORM_*", p->form);
-  if (p->rule < LDPC_RULE_PLAIN || p->rule > LDPC_RULE_NORMALIZED)
+  if (p->rule < LDPC_RULE_PLAIN || p->rule > LDPC_RULE_SUM_PRODUCT)
     return fail(LDPC_ERR_INVALID_ARG, "rule %d is not a known LDPC_RULE_*", p->rule);
+  if (p->rule == LDPC_RULE_SUM_PRODUCT &&
+      (p->dtype != LDPC_DTYPE_F32 || p->form != LDPC_FORM_SS_FIXED || p->schedule != LDPC_SCHEDULE_FLOODING))
+    return fail(LDPC_ERR_UNSUPPORTED, "the sum-product rule runs on the float32 path, SS_FIXED form, flooding");
   if (p->max_iter < 0) return fail(LDPC_ERR_INVALID_ARG, "max_iter %d < 0", p->max_iter);
   if (p->early_stop != 0 && p->early_stop != 1)
     return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");

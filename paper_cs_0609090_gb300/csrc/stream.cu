@@ -489,6 +489,76 @@ __device__ __forceinline__ uint32_t f32s_check(const DevCode& c, const F32Rule& 
   return par;
 }
 
+// The sum-product check rule on per-edge messages: for every position the
+// product of the other inputs' signs times phi(sum over the other positions of
+// phi(min(|u|, 30))), phi(x) = ln(1 + 2 / (e^x - 1)) = -ln tanh(x/2) (phi(0) =
+// inf, phi(inf) = 0 fall out of the formula).  The sum over the other positions
+// is the total minus the position's own term, except for the position with the
+// largest term, whose sum of the others is accumulated separately (the
+// subtraction would cancel there).
+__device__ __forceinline__ float spa_phi(float x) { return log1pf(2.0f / expm1f(x)); }
+
+template <bool ES>
+__device__ __forceinline__ uint32_t f32s_check_spa(const DevCode& c, int m, int f, const F32S& s) {
+  const size_t FL = (size_t)s.FL;
+  const int e0 = __ldg(c.rp + m);
+  const int d = __ldg(c.rp + m + 1) - e0;
+  float total = 0.0f, top = -1.0f, rest = 0.0f;
+  int jtop = 0;
+  uint32_t neg = 0, zero = 0, par = 0;
+  for (int j = 0; j < d; ++j) {
+    const int n = __ldg(c.ci + e0 + j);
+    const float z = s.z[(size_t)n * FL + f];
+    const float u = z - s.lm[(size_t)(e0 + j) * FL + f];
+    if (ES) par ^= (z <= 0.0f) ? 1u : 0u;
+    neg |= (u < 0.0f ? 1u : 0u) << j;
+    zero += (u == 0.0f) ? 1u : 0u;
+    const float ph = spa_phi(fminf(fabsf(u), 30.0f));
+    total += ph;
+    if (ph > top) {
+      if (top >= 0.0f) rest += top;
+      top = ph;
+      jtop = j;
+    } else {
+      rest += ph;
+    }
+  }
+  const uint32_t par_neg = __popc(neg) & 1u;
+  for (int j = 0; j < d; ++j) {
+    const int n = __ldg(c.ci + e0 + j);
+    float l;
+    const float u = s.z[(size_t)n * FL + f] - s.lm[(size_t)(e0 + j) * FL + f];
+    // a zero input among the others makes the message zero
+    if (zero > (u == 0.0f ? 1u : 0u)) {
+      l = 0.0f;
+    } else {
+      const float others = (j == jtop) ? rest : total - spa_phi(fminf(fabsf(u), 30.0f));
+      const float mag = spa_phi(others);
+      l = ((par_neg ^ ((neg >> j) & 1u)) != 0u) ? -mag : mag;
+    }
+    atomicAdd(s.acc + (size_t)n * FL + f, l);
+    s.lm[(size_t)(e0 + j) * FL + f] = l;
+  }
+  return par;
+}
+
+template <bool ES>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_rows_spa(const DevCode c, F32S s, int k) {
+  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = s.FL / 32;
+  const int chunk = warp % n_chunks;
+  const int m0 = (warp / n_chunks) * kRowsPerWarp;
+  if (m0 >= c.M) return;
+  const int f = chunk * 32 + lane;
+  const int cur = k & 1;
+  if (__all_sync(0xffffffffu, s.act[cur * s.FL + f] == 0u)) return;
+  uint32_t fail = 0;
+  const int m1 = min(m0 + kRowsPerWarp, c.M);
+  for (int m = m0; m < m1; ++m) fail |= f32s_check_spa<ES>(c, m, f, s);
+  if (ES && fail) atomicOr(s.fail + cur * s.FL + f, 1u);
+}
+
 template <int FORM, bool ES>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_rows(const DevCode c, const F32Rule r, F32S s, int k) {
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -627,7 +697,8 @@ cudaError_t f32s_run(const DevCode& c, const F32Rule& r, const StreamLayout& L, 
   const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
                    L.lanes / 32);
   for (int k = 1; k <= max_iter; ++k) {
-    f32s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+    if (FORM == 0 && r.rule == 3) f32s_rows_spa<ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, s, k);
+    else f32s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
     f32s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k);
   }
   return cudaGetLastError();

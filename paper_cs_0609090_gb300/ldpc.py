@@ -22,11 +22,12 @@ _lib = ctypes.CDLL(LIB_PATH)
 LDPC_OK, LDPC_ERR_INVALID_ARG, LDPC_ERR_UNSUPPORTED, LDPC_ERR_CUDA, LDPC_ERR_OOM, LDPC_ERR_TIMEOUT = range(6)
 LDPC_DTYPE_INT8, LDPC_DTYPE_F32 = 0, 1
 LDPC_FORM_SS_FIXED, LDPC_FORM_SS_1BIT, LDPC_FORM_TWO_SCAN = 0, 1, 2
-LDPC_RULE_PLAIN, LDPC_RULE_OFFSET, LDPC_RULE_NORMALIZED = 0, 1, 2
+LDPC_RULE_PLAIN, LDPC_RULE_OFFSET, LDPC_RULE_NORMALIZED, LDPC_RULE_SUM_PRODUCT = 0, 1, 2, 3
 
 DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_F32}
 FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
-RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED}
+RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED,
+         "sum_product": LDPC_RULE_SUM_PRODUCT}
 LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM, LDPC_KERNEL_CLUSTER = range(5)
 LDPC_SCHEDULE_FLOODING, LDPC_SCHEDULE_LAYERED = 0, 1
 SCHEDULES = {"flooding": LDPC_SCHEDULE_FLOODING, "layered": LDPC_SCHEDULE_LAYERED}
