@@ -83,3 +83,22 @@ def test_rejected_outside_the_float_per_edge_path(L):
             x = torch.from_numpy(w.q0).cuda()
             L.decode(h, x if kw["dtype"] == "int8" else x.float(), L.make_params(rule="sum_product", **kw))
         assert e.value.status == L.LDPC_ERR_UNSUPPORTED
+
+
+def test_fer_tool_counts_errors_against_the_decoder_outputs(L):
+    """paper_cs_0609090_gb300.fer on a few frames: its error count equals the
+    count taken directly from the same decoder on the same device frames."""
+    import torch
+    from paper_cs_0609090_gb300 import fer as fer_mod
+    w = I.make_workload("reg36_n1008", n_frames=1, with_llr=False)
+    code = L.Code.from_inputs(w.code)
+    rate = (w.code.n_vars - w.code.n_checks) / w.code.n_vars
+    params = L.make_params(**w.params)
+    r = fer_mod.fer(code, params, 300, 1.5, rate=rate, delta=w.delta, qc=w.qc, seed=5, batch=128)
+    llr = torch.empty((300, w.code.n_vars), dtype=torch.float32, device="cuda")
+    L.ldpc_awgn_llr_f32(w.code.n_vars, 5, 0, 300, 1.5, 1.5, rate, None, llr)
+    q = torch.empty((300, w.code.n_vars), dtype=torch.int8, device="cuda")
+    L.ldpc_quantize_llr(llr, 300 * w.code.n_vars, w.delta, w.qc, q)
+    bits, iters, _, _ = L.decode(code, q, params)
+    assert r["frames"] == 300 and r["errors"] == int((bits != 0).any(dim=1).sum().item())
+    assert abs(r["mean_iters"] - float(iters.double().mean().item())) < 1e-9
