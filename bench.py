@@ -26,6 +26,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -125,22 +126,39 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {"onchip_h2_kernel": "onchip_h2.cu", "onchip_int8_kernel": "onchip_int8.cu",
+                  "onchip_twoscan_kernel": "onchip_twoscan.cu", "h2s_rows": "stream.cu", "f32s_rows": "stream_f32.cu",
+                  "layered_kernel": "layered_h2.cu"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the translation unit that defines ``kernel`` and of every local
+    header it includes (transitively): the sources its machine code comes from."""
+    csrc = os.path.join(ROOT, "paper_cs_0609090_gb300", "csrc")
+    seen, todo = [], [os.path.join(csrc, KERNEL_SOURCES[kernel])]
+    while todo:
+        f = os.path.normpath(todo.pop(0))
+        if f in seen:
+            continue
+        seen.append(f)
+        for inc in re.findall(r'^#include "([^"]+)"', open(f).read(), flags=re.M):
+            todo.append(os.path.join(os.path.dirname(f), inc))
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_cs_0609090_gb300", "csrc"))):
-        h.update(open(os.path.join(ROOT, "paper_cs_0609090_gb300", "csrc", f), "rb").read())
+    for f in sorted(seen, key=lambda x: os.path.relpath(x, ROOT)):
+        h.update(os.path.relpath(f, ROOT).encode())
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str, workload: str, form: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; otherwise None."""
+    the current sources of that kernel; otherwise None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
     d = json.load(open(p))
     e = d.get(f"{kernel}/{workload}/{form}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -546,6 +564,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=None,
                     help="decode this many frames of the workload instead of its batch (profiling runs)")
+    ap.add_argument("--iters", type=int, default=None,
+                    help="run this many iterations instead of the workload's (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -564,6 +584,8 @@ def main():
 
     w = I.make_workload(args.workload, frame_seed=1 + rank, n_frames=args.frames)
     w.params["early_stop"] = 0
+    if args.iters is not None:
+        w.params["max_iter"] = args.iters
     F, N, K = w.n_frames, w.code.n_vars, w.K
     code = ldpc.Code.from_inputs(w.code, device=local)
     wp = dict(w.params)

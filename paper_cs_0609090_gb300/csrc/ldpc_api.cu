@@ -229,7 +229,9 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
   if (p->dtype == LDPC_DTYPE_F32 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED) &&
       (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM)) {
     ch->kind = Choice::STREAM_F32;
-    ch->stream = ldpc::stream_layout(1, p->form == LDPC_FORM_SS_1BIT ? 1 : 0, c->N, c->M, c->E, n_frames);
+    // per-edge slots: the degree-sorted table's (min-sum) or the edges of H (sum-product)
+    ch->stream = ldpc::stream_layout(1, p->form == LDPC_FORM_SS_1BIT ? 1 : 0, c->N, c->M,
+                                     std::max(c->E, c->ell_w * c->M), n_frames);
     ch->ws = ch->stream.total;
     return LDPC_OK;
   }

@@ -9,32 +9,33 @@
 //     L + 128 per edge slot j M + m of the degree-sorted table; by CSR edge in
 //     the fallback kernel),
 //     q0 [N][FP] u16 (int8 pair), act/fail [2][FP] u32 bit masks, iters [2 FP]
-//   float path, lane = frame:
-//     Z [N][FL] f32, Acc [N][FL] f32, state [M][FL] uint4 {A, B, n~, signs} or
-//     [E][FL] f32, q0 [N][FL] f32, act/fail [2][FL] u32, iters [FL]
+//   float path (stream_f32.cu), lane = frame:
+//     Z [2][N][FL] f32 (two posterior buffers), state [M][FL] uint4
+//     {A, B, n~, signs} or per-edge f32, q0 [N][FL] f32, act/fail [2][FL] u32,
+//     iters [FL]
 // Per iteration: a row kernel (one warp = one check for 32 lanes of frames; the
 // check's column indices are warp-uniform loads) then a column kernel that
 // applies the stop rule.  int8: the row kernel adds L^(k) - L^(k-1) to an
 // accumulator that always holds the current posterior (exact integer sums), so
 // the column kernel only converts it for the frames that continue; the CSR
 // fallback adds L^(k) and the column kernel resets the accumulator to Z0.  The
-// syndrome of x^(k-1) is computed by the row kernel of iteration k.  The float accumulation uses
-// floating-point atomics, so its rounding depends on the order of the additions.
+// syndrome of x^(k-1) is computed by the row kernel of iteration k.
 #include <algorithm>
 
 #include "h2_body.cuh"
 #include "kernels.h"
+#include "stream_grid.h"
 
 namespace ldpc {
 namespace {
-
-constexpr int kRowsPerWarp = 4;
-constexpr int kWarpsPerBlock = 8;
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// E = message slots of the per-edge form: the degree-sorted table's ell_w * M;
+// float32 is given max(E, ell_w * M), the sum-product rule addressing the E
+// edges of H.  For float32, z and acc are the two posterior buffers.
 StreamLayout stream_layout(int dtype, int form, int N, int M, int E, int F) {
   StreamLayout L;
   const bool f32 = dtype == 1;
@@ -270,12 +271,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
       asm volatile("prefetch.global.L1 [%0];" ::"l"(St + ad.st(m + 1)));
     }
     using A = StreamAddr<WIDE>;
-    switch (d) {
-      case 6: fail |= check_body<2, FORM, 6, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 7: fail |= check_body<2, FORM, 7, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 14: fail |= check_body<2, FORM, 14, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      case 15: fail |= check_body<2, FORM, 15, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
-      default: fail |= check_body<2, FORM, 0, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+    if constexpr (FORM == 1) {
+      switch (d) {
+        case 6: fail |= check_body<2, FORM, 6, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+        case 7: fail |= check_body<2, FORM, 7, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+        case 14: fail |= check_body<2, FORM, 14, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+        case 15: fail |= check_body<2, FORM, 15, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+        default: fail |= check_body<2, FORM, 0, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      }
+    } else {
+      // (per-edge: more exact-degree bodies here cost the kernel spills)
+      if (d == 6) fail |= check_body<2, FORM, 6, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm);
+      else if (d == 7) fail |= check_body<2, FORM, 7, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm);
+      else fail |= check_body<2, FORM, 0, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm);
     }
   }
   if (ES && fail) atomicOr(s.fail + cur * s.FP + p, fail);
@@ -385,295 +393,6 @@ __global__ void __launch_bounds__(256) h2s_output(const DevCode c, H2S s, int kf
   }
 }
 
-// ------------------------------------------------------------------ float32
-
-struct F32S {
-  float* z;
-  float* acc;
-  uint4* st;
-  float* lm;
-  float* q0;
-  uint32_t* act;
-  uint32_t* fail;
-  int32_t* iters;
-  uint32_t* ok;
-  int FL;
-};
-
-F32S f32s_view(void* ws, const StreamLayout& L) {
-  char* b = static_cast<char*>(ws);
-  F32S s;
-  s.z = reinterpret_cast<float*>(b + L.z);
-  s.acc = reinterpret_cast<float*>(b + L.acc);
-  s.st = reinterpret_cast<uint4*>(b + L.st);
-  s.lm = reinterpret_cast<float*>(b + L.st);
-  s.q0 = reinterpret_cast<float*>(b + L.q0);
-  s.act = reinterpret_cast<uint32_t*>(b + L.act);
-  s.fail = reinterpret_cast<uint32_t*>(b + L.fail);
-  s.iters = reinterpret_cast<int32_t*>(b + L.iters);
-  s.ok = reinterpret_cast<uint32_t*>(b + L.ok);
-  s.FL = L.lanes;
-  return s;
-}
-
-__global__ void __launch_bounds__(256) f32s_init(const DevCode c, const float* __restrict__ llr, int32_t F,
-                                                 int32_t max_iter, F32S s) {
-  __shared__ float tile[32][65];  // [frame][variable]
-  const int n0 = blockIdx.x * 64, f0 = blockIdx.y * 32;
-  const int N = c.N;
-  for (int i = threadIdx.x; i < 32 * 64; i += blockDim.x) {
-    const int fl = i >> 6, nl = i & 63;
-    const int f = f0 + fl, n = n0 + nl;
-    tile[fl][nl] = (f < F && n < N) ? llr[(size_t)f * N + n] : 0.0f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
-    const int nl = i >> 5, fl = i & 31;
-    const int n = n0 + nl;
-    if (n >= N) continue;
-    const size_t o = (size_t)n * s.FL + f0 + fl;
-    const float q = tile[fl][nl];
-    s.q0[o] = q;
-    s.z[o] = q;
-    s.acc[o] = q;
-  }
-  if (blockIdx.x == 0) {
-    for (int fl = threadIdx.x; fl < 32; fl += blockDim.x) {
-      const int f = f0 + fl;
-      s.act[s.FL + f] = f < F ? 1u : 0u;
-      s.act[f] = 0u;
-      s.fail[f] = 0u;
-      s.fail[s.FL + f] = 0u;
-      s.iters[f] = max_iter;
-      s.ok[f] = 0u;
-    }
-  }
-}
-
-template <int FORM, bool ES>
-__device__ __forceinline__ uint32_t f32s_check(const DevCode& c, const F32Rule& r, int m, int f, const F32S& s) {
-  const size_t FL = (size_t)s.FL;
-  const int e0 = __ldg(c.rp + m);
-  const int d = __ldg(c.rp + m + 1) - e0;
-  float A = 0.f, B = 0.f;
-  int I = 0;
-  uint32_t S = 0;
-  if constexpr (FORM == 1) {
-    const uint4 st = s.st[(size_t)m * FL + f];
-    A = __uint_as_float(st.x);
-    B = __uint_as_float(st.y);
-    I = (int)st.z;
-    S = st.w;
-  }
-  float mn1 = __int_as_float(0x7f800000), mn2 = __int_as_float(0x7f800000);
-  int idx = 0;
-  uint32_t neg = 0, par = 0;
-  for (int j = 0; j < d; ++j) {
-    const int n = __ldg(c.ci + e0 + j);
-    const float z = s.z[(size_t)n * FL + f];
-    float lold;
-    if constexpr (FORM == 1) {
-      const float mag = (j == I) ? B : A;
-      lold = ((S >> j) & 1u) ? -mag : mag;
-    } else {
-      lold = s.lm[(size_t)(e0 + j) * FL + f];
-    }
-    if (ES) par ^= (z <= 0.0f) ? 1u : 0u;
-    const float u = z - lold;
-    neg |= (u < 0.0f ? 1u : 0u) << j;
-    const float a = fabsf(u);
-    if (a < mn1) { mn2 = mn1; mn1 = a; idx = j; }
-    else if (a < mn2) { mn2 = a; }
-  }
-  const uint32_t dm = d >= 32 ? 0xffffffffu : ((1u << d) - 1u);
-  const uint32_t Sn = ((__popc(neg) & 1) ? ~neg : neg) & dm;
-  const float An = r.g(mn1), Bn = r.g(mn2);
-  for (int j = 0; j < d; ++j) {
-    const int n = __ldg(c.ci + e0 + j);
-    const float mag = (j == idx) ? Bn : An;
-    const float l = ((Sn >> j) & 1u) ? -mag : mag;
-    atomicAdd(s.acc + (size_t)n * FL + f, l);
-    if constexpr (FORM == 0) s.lm[(size_t)(e0 + j) * FL + f] = l;
-  }
-  if constexpr (FORM == 1)
-    s.st[(size_t)m * FL + f] = make_uint4(__float_as_uint(An), __float_as_uint(Bn), (uint32_t)idx, Sn);
-  return par;
-}
-
-// The sum-product check rule on per-edge messages: for every position the
-// product of the other inputs' signs times phi(sum over the other positions of
-// phi(min(|u|, 30))), phi(x) = ln(1 + 2 / (e^x - 1)) = -ln tanh(x/2) (phi(0) =
-// inf, phi(inf) = 0 fall out of the formula).  The sum over the other positions
-// is the total minus the position's own term, except for the position with the
-// largest term, whose sum of the others is accumulated separately (the
-// subtraction would cancel there).
-__device__ __forceinline__ float spa_phi(float x) { return log1pf(2.0f / expm1f(x)); }
-
-template <bool ES>
-__device__ __forceinline__ uint32_t f32s_check_spa(const DevCode& c, int m, int f, const F32S& s) {
-  const size_t FL = (size_t)s.FL;
-  const int e0 = __ldg(c.rp + m);
-  const int d = __ldg(c.rp + m + 1) - e0;
-  float total = 0.0f, top = -1.0f, rest = 0.0f;
-  int jtop = 0;
-  uint32_t neg = 0, zero = 0, par = 0;
-  for (int j = 0; j < d; ++j) {
-    const int n = __ldg(c.ci + e0 + j);
-    const float z = s.z[(size_t)n * FL + f];
-    const float u = z - s.lm[(size_t)(e0 + j) * FL + f];
-    if (ES) par ^= (z <= 0.0f) ? 1u : 0u;
-    neg |= (u < 0.0f ? 1u : 0u) << j;
-    zero += (u == 0.0f) ? 1u : 0u;
-    const float ph = spa_phi(fminf(fabsf(u), 30.0f));
-    total += ph;
-    if (ph > top) {
-      if (top >= 0.0f) rest += top;
-      top = ph;
-      jtop = j;
-    } else {
-      rest += ph;
-    }
-  }
-  const uint32_t par_neg = __popc(neg) & 1u;
-  for (int j = 0; j < d; ++j) {
-    const int n = __ldg(c.ci + e0 + j);
-    float l;
-    const float u = s.z[(size_t)n * FL + f] - s.lm[(size_t)(e0 + j) * FL + f];
-    // a zero input among the others makes the message zero
-    if (zero > (u == 0.0f ? 1u : 0u)) {
-      l = 0.0f;
-    } else {
-      const float others = (j == jtop) ? rest : total - spa_phi(fminf(fabsf(u), 30.0f));
-      const float mag = spa_phi(others);
-      l = ((par_neg ^ ((neg >> j) & 1u)) != 0u) ? -mag : mag;
-    }
-    atomicAdd(s.acc + (size_t)n * FL + f, l);
-    s.lm[(size_t)(e0 + j) * FL + f] = l;
-  }
-  return par;
-}
-
-template <bool ES>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_rows_spa(const DevCode c, F32S s, int k) {
-  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FL / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
-  const int f = chunk * 32 + lane;
-  const int cur = k & 1;
-  if (__all_sync(0xffffffffu, s.act[cur * s.FL + f] == 0u)) return;
-  uint32_t fail = 0;
-  const int m1 = min(m0 + kRowsPerWarp, c.M);
-  for (int m = m0; m < m1; ++m) fail |= f32s_check_spa<ES>(c, m, f, s);
-  if (ES && fail) atomicOr(s.fail + cur * s.FL + f, 1u);
-}
-
-template <int FORM, bool ES>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_rows(const DevCode c, const F32Rule r, F32S s, int k) {
-  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FL / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
-  const int f = chunk * 32 + lane;
-  const int cur = k & 1;
-  if (__all_sync(0xffffffffu, s.act[cur * s.FL + f] == 0u)) return;
-  uint32_t fail = 0;
-  const int m1 = min(m0 + kRowsPerWarp, c.M);
-  for (int m = m0; m < m1; ++m) fail |= f32s_check<FORM, ES>(c, r, m, f, s);
-  if (ES && fail) atomicOr(s.fail + cur * s.FL + f, 1u);
-}
-
-template <bool ES>
-__global__ void __launch_bounds__(256) f32s_cols(const DevCode c, F32S s, int k) {
-  const int f = blockIdx.y * 32 + (threadIdx.x & 31);
-  const int cur = k & 1, nxt = cur ^ 1;
-  const uint32_t act = s.act[cur * s.FL + f];
-  const uint32_t stop = ES ? (act & (s.fail[cur * s.FL + f] ^ 1u)) : 0u;
-  const uint32_t cont = act & ~stop;
-  for (int n = blockIdx.x * 8 + (threadIdx.x >> 5); n < c.N; n += gridDim.x * 8) {
-    const size_t o = (size_t)n * s.FL + f;
-    if (cont) s.z[o] = s.acc[o];
-    s.acc[o] = s.q0[o];
-  }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    s.act[nxt * s.FL + f] = cont;
-    s.fail[nxt * s.FL + f] = 0u;
-    if (ES && stop) {
-      s.iters[f] = k - 1;
-      s.ok[f] = 1u;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_final_syndrome(const DevCode c, F32S s, int kf) {
-  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FL / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
-  const int f = chunk * 32 + lane;
-  const int cur = kf & 1;
-  if (__all_sync(0xffffffffu, s.act[cur * s.FL + f] == 0u)) return;
-  uint32_t fail = 0;
-  const int m1 = min(m0 + kRowsPerWarp, c.M);
-  for (int m = m0; m < m1; ++m) {
-    uint32_t y = 0;
-    for (int e = __ldg(c.rp + m); e < __ldg(c.rp + m + 1); ++e)
-      y ^= (s.z[(size_t)__ldg(c.ci + e) * s.FL + f] <= 0.0f) ? 1u : 0u;
-    fail |= y;
-  }
-  if (fail) atomicOr(s.fail + cur * s.FL + f, 1u);
-}
-
-__global__ void __launch_bounds__(256) f32s_output(const DevCode c, F32S s, int kf, int32_t F, uint8_t* bits,
-                                                   int32_t* iters, uint8_t* okf, float* zout) {
-  __shared__ float tile[64][33];  // [variable][frame]
-  const int n0 = blockIdx.x * 64, f0 = blockIdx.y * 32;
-  const int N = c.N, N8 = (N + 7) >> 3;
-  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
-    const int nl = i >> 5, fl = i & 31;
-    const int n = n0 + nl;
-    tile[nl][fl] = n < N ? s.z[(size_t)n * s.FL + f0 + fl] : 0.0f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 32 * 8; i += blockDim.x) {
-    const int fl = i >> 3, bl = i & 7;
-    const int f = f0 + fl, b = (n0 >> 3) + bl;
-    if (f >= F || b >= N8) continue;
-    uint32_t byte = 0;
-    for (int t = 0; t < 8; ++t) {
-      const int nl = bl * 8 + t;
-      if (n0 + nl < N) byte |= (tile[nl][fl] <= 0.0f ? 1u : 0u) << t;
-    }
-    bits[(size_t)f * N8 + b] = (uint8_t)byte;
-  }
-  if (zout != nullptr) {
-    for (int i = threadIdx.x; i < 32 * 64; i += blockDim.x) {
-      const int fl = i >> 6, nl = i & 63;
-      const int f = f0 + fl, n = n0 + nl;
-      if (f < F && n < N) zout[(size_t)f * N + n] = tile[nl][fl];
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    const int f = f0 + threadIdx.x;
-    if (f < F) {
-      const int cur = kf & 1;
-      const bool running = s.act[cur * s.FL + f] != 0u;
-      iters[f] = s.iters[f];
-      okf[f] = running ? (uint8_t)(s.fail[cur * s.FL + f] ^ 1u) : (uint8_t)s.ok[f];
-    }
-  }
-}
-
-int rows_grid(int M, int lanes) {
-  const int64_t warps = (int64_t)((M + kRowsPerWarp - 1) / kRowsPerWarp) * (lanes / 32);
-  return (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-}
 
 // Per iteration: the degree-sorted row kernel with delta accumulation and the
 // converting column kernel (delta == true), or the CSR row kernel with the
@@ -697,20 +416,6 @@ cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H
       h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
       h2s_cols<ES, false><<<cgrid, 256, 0, st>>>(c, s, k);
     }
-  }
-  return cudaGetLastError();
-}
-
-template <int FORM, bool ES>
-cudaError_t f32s_run(const DevCode& c, const F32Rule& r, const StreamLayout& L, F32S s, int sm_count,
-                     int32_t max_iter, cudaStream_t st) {
-  const int rgrid = rows_grid(c.M, L.lanes);
-  const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
-                   L.lanes / 32);
-  for (int k = 1; k <= max_iter; ++k) {
-    if (FORM == 0 && r.rule == 3) f32s_rows_spa<ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, s, k);
-    else f32s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
-    f32s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k);
   }
   return cudaGetLastError();
 }
@@ -739,27 +444,6 @@ cudaError_t stream_int8_decode(const DevCode& c, const IntRule& r, int form, con
   const int kf = max_iter + 1;
   h2s_final_syndrome<<<rows_grid(c.M, L.lanes), kWarpsPerBlock * 32, 0, st>>>(c, s, kf);
   h2s_output<<<tgrid, 256, 0, st>>>(c, s, kf, F, bits, iters, ok, zout);
-  return cudaGetLastError();
-}
-
-cudaError_t stream_f32_decode(const DevCode& c, const F32Rule& r, int form, const StreamLayout& L, void* ws,
-                              int sm_count, const float* llr, int32_t F, int32_t max_iter, int32_t early_stop,
-                              uint8_t* bits, int32_t* iters, uint8_t* ok, float* zout, cudaStream_t st) {
-  F32S s = f32s_view(ws, L);
-  const dim3 tgrid((c.N + 63) / 64, L.lanes / 32);
-  cudaError_t e0 = cudaMemsetAsync(static_cast<char*>(ws) + L.st, 0, L.q0 - L.st, st);  // L^(0) = 0
-  if (e0 != cudaSuccess) return e0;
-  f32s_init<<<tgrid, 256, 0, st>>>(c, llr, F, max_iter, s);
-  cudaError_t e;
-  const bool es = early_stop != 0;
-  if (form == 1) e = es ? f32s_run<1, true>(c, r, L, s, sm_count, max_iter, st)
-                        : f32s_run<1, false>(c, r, L, s, sm_count, max_iter, st);
-  else e = es ? f32s_run<0, true>(c, r, L, s, sm_count, max_iter, st)
-              : f32s_run<0, false>(c, r, L, s, sm_count, max_iter, st);
-  if (e != cudaSuccess) return e;
-  const int kf = max_iter + 1;
-  f32s_final_syndrome<<<rows_grid(c.M, L.lanes), kWarpsPerBlock * 32, 0, st>>>(c, s, kf);
-  f32s_output<<<tgrid, 256, 0, st>>>(c, s, kf, F, bits, iters, ok, zout);
   return cudaGetLastError();
 }
 

@@ -139,6 +139,59 @@ def test_f32_early_stop_regular(L, form, rule, offset):
     assert err.max() <= tol, f"max relative error {err.max():.3g}"
 
 
+def _clean_parity(g, o, rtol, min_clean=0.9):
+    """Iterations, flags and decisions equal on the frames away from the decision
+    boundary; posteriors of the decoded ones within rtol of the FP64 oracle."""
+    clean = o.margin >= MARGIN
+    assert clean.sum() >= min_clean * clean.size, f"{(~clean).sum()} near-tie frames"
+    for key in ("iters", "ok", "bits"):
+        assert np.array_equal(g[key][clean], o[key][clean]), key
+    conv = clean & (o.ok == 1)
+    if conv.any():
+        err = np.abs(g["z"][conv] - o.z[conv]) / np.maximum(1.0, np.abs(o.z[conv]))
+        assert err.max() <= rtol, f"max relative error {err.max():.3g}"
+    return clean
+
+
+@pytest.mark.parametrize("form", FORMS_INT)
+def test_f32_edge_cases(L, form):
+    """One frame and ragged frame counts (the lanes of the last warp partly
+    empty), max_iter = 0 (the channel values returned as they are), and noiseless
+    frames (stopped at iteration 0 from the first posterior buffer)."""
+    w = I.make_workload("reg36_n1008", n_frames=65, ebn0_db=2.0, frame_seed=5)
+    for F in (1, 33, 65):
+        g, o = _f32(L, w.code, w.llr[:F], form, "normalized", max_iter=30, early_stop=1)
+        _clean_parity(g, o, RTOL, min_clean=0.8)
+    g, o = _f32(L, w.code, w.llr[:7], form, "normalized", max_iter=0, early_stop=1)
+    assert np.array_equal(g["z"], w.llr[:7].astype(np.float32))
+    assert np.all(g["iters"] == 0)
+    assert np.array_equal(g["ok"], o.ok) and np.array_equal(g["bits"], o.bits)
+    q = I.noiseless(w.codewords[:3], 31).astype(np.float32)
+    g, o = _f32(L, w.code, q, form, "normalized", max_iter=30, early_stop=1)
+    assert np.all(g["iters"] == 0) and np.all(g["ok"] == 1) and np.array_equal(g["z"], q)
+
+
+@pytest.mark.parametrize("form", FORMS_INT)
+def test_f32_other_degrees(L, form):
+    """Row degree 9 (the kernel's loop body) and the quasi-cyclic code's degrees
+    14 / 15 (unrolled bodies in the Section V form), with frames stopping at odd
+    and even iteration counts, whose results come from different posterior
+    buffers."""
+    code = I.regular_code(990, 3, 9, seed=5)
+    zero = np.zeros((160, code.n_vars), np.uint8)
+    llr = I.awgn_llr(zero, 3.2, 2.0 / 3.0, seed=17)
+    g, o = _f32(L, code, llr, form, "normalized", max_iter=25, early_stop=1)
+    clean = _clean_parity(g, o, RTOL, min_clean=0.8)
+    assert len(set((g["iters"][clean] % 2).tolist())) == 2
+    w = I.make_workload("qc_n7493", n_frames=96, ebn0_db=3.3, frame_seed=6)
+    g, o = _f32(L, w.code, w.llr, form, "normalized", max_iter=25, early_stop=1)
+    clean = _clean_parity(g, o, RTOL, min_clean=0.8)
+    assert len(set((g["iters"][clean] % 2).tolist())) == 2
+    g, o = _f32(L, w.code, w.llr[:40], form, "offset", offset=0.25, max_iter=12, early_stop=0)
+    err = np.abs(g["z"] - o.z) / np.maximum(1.0, np.abs(o.z))
+    assert err.max() <= RTOL_OFFSET, f"max relative error {err.max():.3g}"
+
+
 def test_stream_workspace_contract(L):
     import torch
     w = I.make_workload("irr_n64800", n_frames=2)
