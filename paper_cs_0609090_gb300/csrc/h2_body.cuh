@@ -120,13 +120,19 @@ __device__ __forceinline__ uint32_t row_parity_body(const Addr& ad, const uint16
 //       position j of the even frame at bit 15 - j, of the odd frame at bit
 //       31 - j, so that shifting the word left by j (a running S + S) brings both
 //       to the binary16 sign bits}
+//       C8 (checks of degree <= 8, magnitudes <= 255): 8 bytes per frame pair,
+//       the size of Section V's state, [rows][P] uint2 (St then addresses uint2
+//       entries) {A_even, A_odd, B_even, B_odd as bytes; n~_even | signs_even
+//       << 8 | n~_odd << 16 | signs_odd << 24}: the sign bytes sit where the
+//       16-byte form keeps them, and the bytes below them are never shifted up
+//       to a sign bit within 8 positions
 //   Lm  (FORM 0) [ell_w][rows][P] u16: L + 128 per frame (one byte each)
 //   ACC: how the new messages reach the posteriors.  0: add L^(k) into the
 //       accumulator; 1: add L^(k) - L^(k-1) (an accumulator that holds Z^(k-1)
 //       and is never reset; the streaming kernels); 2: update the posterior in
 //       place, Z_n <- Z_n + L^(k) - L^(k-1), through Addr::update (the layered
 //       schedule, where the checks running together share no variable)
-template <int G, int FORM, int D, int DMAX, bool ES, class Addr, int ACC = 0>
+template <int G, int FORM, int D, int DMAX, bool ES, class Addr, int ACC = 0, bool C8 = false>
 __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* __restrict__ tab,
                                                const uint32_t* __restrict__ Zs, int32_t* __restrict__ Acc,
                                                const H2Rule& rule, uint32_t qm2, int m, int d,
@@ -137,15 +143,25 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
   // need those registers for state and reload them
   constexpr bool KEEP = (P == 1 && FORM == 1 && !ES && ACC != 2);
   using H = typename Addr::H;
+  static_assert(!C8 || (FORM == 1 && DMAX <= 8 && D <= 8), "the 8-byte state holds checks of degree <= 8");
   uint32_t A2[P], B2[P], I2[P], S[P];
   if constexpr (FORM == 1) {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      const uint4 s = St[ad.st(m) + p];
-      A2[p] = s.x;
-      B2[p] = s.y;
-      I2[p] = s.z;
-      S[p] = s.w;
+      if constexpr (C8) {
+        // byte b -> binary16 pattern 0x6400 + b = 1024 + b, minus 1024: exact
+        const uint2 s = reinterpret_cast<const uint2*>(St)[ad.st(m) + p];
+        A2[p] = hsub(__byte_perm(s.x, 0x64u, 0x4140), 0x64006400u);
+        B2[p] = hsub(__byte_perm(s.x, 0x64u, 0x4342), 0x64006400u);
+        I2[p] = hsub(__byte_perm(s.y, 0x64u, 0x4240), 0x64006400u);
+        S[p] = s.y;
+      } else {
+        const uint4 s = St[ad.st(m) + p];
+        A2[p] = s.x;
+        B2[p] = s.y;
+        I2[p] = s.z;
+        S[p] = s.w;
+      }
     }
   }
   uint32_t K1[P], K2[P], NEG[P], Y[P], SR[P], D2[P];
@@ -202,6 +218,7 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
   const int dd = D > 0 ? D : d;
   const uint32_t dlane = ((1u << dd) - 1u) << (16 - dd);  // bits 16-d .. 15
   uint32_t An[P], Bn[P], In[P], Sn[P];
+  uint32_t W0[C8 ? P : 1], W1[C8 ? P : 1];
   uint32_t par = 0;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
@@ -211,9 +228,15 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
     Sn[p] = (NEG[p] ^ pm) & (dlane | (dlane << 16));
     const int32_t k1l = h_lo_int(K1[p]), k1h = h_hi_int(K1[p]);
     const int32_t k2l = h_lo_int(K2[p]), k2h = h_hi_int(K2[p]);
-    An[p] = small_to_h2(rule.g(k1l >> 4), rule.g(k1h >> 4));
-    Bn[p] = small_to_h2(rule.g(k2l >> 4), rule.g(k2h >> 4));
+    const int32_t al = rule.g(k1l >> 4), ah = rule.g(k1h >> 4);
+    const int32_t bl = rule.g(k2l >> 4), bh = rule.g(k2h >> 4);
+    An[p] = small_to_h2(al, ah);
+    Bn[p] = small_to_h2(bl, bh);
     In[p] = small_to_h2(k1l & 15, k1h & 15);
+    if constexpr (C8) {
+      W0[p] = (uint32_t)al | ((uint32_t)ah << 8) | ((uint32_t)bl << 16) | ((uint32_t)bh << 24);
+      W1[p] = (uint32_t)(k1l & 15) | ((uint32_t)(k1h & 15) << 16) | (Sn[p] & 0xff00ff00u);
+    }
     if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
   }
 
@@ -270,7 +293,10 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
   }
   if constexpr (FORM == 1) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) St[ad.st(m) + p] = make_uint4(An[p], Bn[p], In[p], Sn[p]);
+    for (int p = 0; p < P; ++p) {
+      if constexpr (C8) reinterpret_cast<uint2*>(St)[ad.st(m) + p] = make_uint2(W0[p], W1[p]);
+      else St[ad.st(m) + p] = make_uint4(An[p], Bn[p], In[p], Sn[p]);
+    }
   }
   return par;
 }

@@ -198,10 +198,8 @@ template <int FORM, bool ES>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) h2s_rows(const DevCode c, const IntRule r, H2S s, int k) {
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FP / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
+  int chunk, m0;
+  if (!row_map_all(warp, c.M, s.FP, chunk, m0)) return;
   const int p = chunk * 32 + lane;
   const int cur = k & 1;
   if (__all_sync(0xffffffffu, s.act[cur * s.FP + p] == 0u)) return;
@@ -236,15 +234,18 @@ struct StreamAddr {
 // Row pass with the exact-degree bodies: one warp = kRowsPerWarp consecutive
 // checks of the degree-sorted order for 32 frame pairs.  Per-edge messages are
 // kept per edge slot (j * M + internal check).  Offsets are 32-bit (the host
-// checks N FP and ell_w M FP < 2^32).
-template <int FORM, bool ES, bool WIDE, int MINB, bool DELTA>
+// checks N FP and ell_w M FP < 2^32).  C8: the Section V state in 8 bytes per
+// frame pair (codes whose checks all have degree <= 8).
+template <int FORM, bool ES, bool WIDE, int MINB, bool DELTA, bool C8 = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const DevCode c, const IntRule r, H2S s, int k) {
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FP / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
+  int chunk, m0;
+  if constexpr (FORM == 1) {
+    if (!row_map<kChunksSV>(blockIdx.x, blockIdx.y, threadIdx.x >> 5, c.M, s.FP, chunk, m0)) return;
+  } else {
+    if (!row_map_all(warp, c.M, s.FP, chunk, m0)) return;
+  }
   const int p = chunk * 32 + lane;
   const int cur = k & 1;
   if (__all_sync(0xffffffffu, s.act[cur * s.FP + p] == 0u)) return;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
   const StreamAddr<WIDE> ad{c.M, (uint32_t)s.FP, c.ell16, c.ell32};
   const uint32_t* Zs = s.z + p;
   int32_t* Acc = s.acc + p;
-  uint4* St = s.st + p;
+  uint4* St = C8 ? reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(s.st) + p) : s.st + p;
   uint16_t* Lm = s.lm + p;
   uint32_t fail = 0;
   const int m1 = min(m0 + kRowsPerWarp, c.M);
@@ -268,10 +269,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
         const uint32_t h = ad.at(nullptr, nullptr, j, m + 1);
         asm volatile("prefetch.global.L1 [%0];" ::"l"(Zs + h));
       }
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(St + ad.st(m + 1)));
+      const void* sn = C8 ? static_cast<const void*>(reinterpret_cast<const uint2*>(St) + ad.st(m + 1))
+                          : static_cast<const void*>(St + ad.st(m + 1));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(sn));
     }
     using A = StreamAddr<WIDE>;
-    if constexpr (FORM == 1) {
+    if constexpr (C8) {
+      switch (d) {
+        case 6: fail |= check_body<2, 1, 6, 8, ES, A, DELTA ? 1 : 0, true>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+        case 7: fail |= check_body<2, 1, 7, 8, ES, A, DELTA ? 1 : 0, true>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+        default: fail |= check_body<2, 1, 0, 8, ES, A, DELTA ? 1 : 0, true>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
+      }
+    } else if constexpr (FORM == 1) {
       switch (d) {
         case 6: fail |= check_body<2, FORM, 6, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
         case 7: fail |= check_body<2, FORM, 7, 16, ES, A, DELTA ? 1 : 0>(ad, nullptr, Zs, Acc, hr, qm2, m, d, St, Lm); break;
@@ -328,10 +337,8 @@ __global__ void __launch_bounds__(256) h2s_cols(const DevCode c, H2S s, int k) {
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) h2s_final_syndrome(const DevCode c, H2S s, int kf) {
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FP / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
+  int chunk, m0;
+  if (!row_map_all(warp, c.M, s.FP, chunk, m0)) return;
   const int p = chunk * 32 + lane;
   const int cur = kf & 1;
   if (__all_sync(0xffffffffu, s.act[cur * s.FP + p] == 0u)) return;
@@ -404,13 +411,21 @@ template <int FORM, bool ES>
 cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H2S s, int sm_count,
                     int32_t max_iter, bool delta, cudaStream_t st) {
   const int rgrid = rows_grid(c.M, L.lanes);
+  // the degree-sorted kernel: Section V form on a 2-D grid (chunk groups),
+  // per-edge form on the 1-D check-major grid
+  const RowGrid g2 = rows_grid_g(c.M, L.lanes, kChunksSV);
+  const dim3 egrid = FORM == 1 ? dim3((unsigned)g2.x, (unsigned)g2.y) : dim3((unsigned)rgrid);
   const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
                    L.lanes / 32);
   const bool wide = c.ell16 == nullptr;
+  const bool c8 = c.ell_w <= 8;  // every check of degree <= 8: the 8-byte Section V state
   for (int k = 1; k <= max_iter; ++k) {
     if (delta) {
-      if (wide) h2s_rows_ell<FORM, ES, true, 4, true><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
-      else h2s_rows_ell<FORM, ES, false, 4, true><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+      if (FORM == 1 && c8) {
+        if (wide) h2s_rows_ell<1, ES, true, 4, true, true><<<egrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+        else h2s_rows_ell<1, ES, false, 4, true, true><<<egrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+      } else if (wide) h2s_rows_ell<FORM, ES, true, 4, true><<<egrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+      else h2s_rows_ell<FORM, ES, false, 4, true><<<egrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
       h2s_cols<ES, true><<<cgrid, 256, 0, st>>>(c, s, k);
     } else {
       h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);

@@ -96,10 +96,14 @@ __global__ void __launch_bounds__(256) f32s_init(const DevCode c, const float* _
 // first position of min1 and the sign parity, and add L^(k)_mn into Zn.  With
 // D > 0 the degree is D and the loops are unrolled, so that the check's table
 // and posterior loads are all in flight together; D = 0 takes the degree d.
-template <int FORM, bool ES, int D, bool WIDE>
+// C8 (checks of degree <= 8): the state in 10 bytes per frame, the size of
+// Section V's float form: {A, B} in St (uint2 entries) and n~ | signs << 8 in Sx.
+template <int FORM, bool ES, int D, bool WIDE, bool C8 = false>
 __device__ __forceinline__ uint32_t f32s_check_ell(const DevCode& c, const F32Rule& r, int m, int d, size_t FL,
                                                    const float* __restrict__ Zp, float* __restrict__ Zn,
-                                                   uint4* __restrict__ St, float* __restrict__ Lm) {
+                                                   uint4* __restrict__ St, uint16_t* __restrict__ Sx,
+                                                   float* __restrict__ Lm) {
+  static_assert(!C8 || (FORM == 1 && D <= 8), "the 10-byte state holds checks of degree <= 8");
   const int M = c.M;
   auto col = [&](int j) -> int {
     return WIDE ? __ldg(c.ell32 + (size_t)j * M + m) : (int)__ldg(c.ell16 + (size_t)j * M + m);
@@ -107,7 +111,14 @@ __device__ __forceinline__ uint32_t f32s_check_ell(const DevCode& c, const F32Ru
   float A = 0.f, B = 0.f;
   int I = 0;
   uint32_t S = 0;
-  if constexpr (FORM == 1) {
+  if constexpr (FORM == 1 && C8) {
+    const uint2 ab = reinterpret_cast<const uint2*>(St)[(size_t)m * FL];
+    const uint32_t is = Sx[(size_t)m * FL];
+    A = __uint_as_float(ab.x);
+    B = __uint_as_float(ab.y);
+    I = (int)(is & 0xffu);
+    S = is >> 8;
+  } else if constexpr (FORM == 1) {
     const uint4 st = St[(size_t)m * FL];
     A = __uint_as_float(st.x);
     B = __uint_as_float(st.y);
@@ -159,22 +170,25 @@ __device__ __forceinline__ uint32_t f32s_check_ell(const DevCode& c, const F32Ru
   } else {
     for (int j = 0; j < d; ++j) emit(j, col(j));
   }
-  if constexpr (FORM == 1)
+  if constexpr (FORM == 1 && C8) {
+    reinterpret_cast<uint2*>(St)[(size_t)m * FL] = make_uint2(__float_as_uint(An), __float_as_uint(Bn));
+    Sx[(size_t)m * FL] = (uint16_t)((uint32_t)idx | (Sn << 8));
+  } else if constexpr (FORM == 1) {
     St[(size_t)m * FL] = make_uint4(__float_as_uint(An), __float_as_uint(Bn), (uint32_t)idx, Sn);
+  }
   return par;
 }
 
 // Row pass of iteration k: one warp = kRowsPerWarp consecutive internal checks
-// for 32 frames.
-template <int FORM, bool ES, bool WIDE>
+// for 32 frames.  C8: the 10-byte state, {A, B} as [M][FL] uint2 followed by
+// [M][FL] u16 {n~, signs} in the state region.
+template <int FORM, bool ES, bool WIDE, bool C8 = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) f32s_rows_ell(const DevCode c, const F32Rule r, F32S s,
                                                                          int k) {
-  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FL / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
+  int chunk, m0;
+  if (!row_map<FORM == 1 ? kChunksSV : kChunksF32PE>(blockIdx.x, blockIdx.y, threadIdx.x >> 5, c.M, s.FL, chunk, m0))
+    return;
   const int f = chunk * 32 + lane;
   const int cur = k & 1;
   const bool active = s.act[cur * s.FL + f] != 0u;
@@ -183,24 +197,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) f32s_rows_ell(const De
   const size_t FL = (size_t)s.FL;
   const float* Zp = s.zb(k - 1) + f;
   float* Zn = s.zb(k) + f;
-  uint4* St = s.st + f;
+  uint4* St = C8 ? reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(s.st) + f) : s.st + f;
+  uint16_t* Sx = reinterpret_cast<uint16_t*>(reinterpret_cast<uint2*>(s.st) + (size_t)c.M * FL) + f;
   float* Lm = s.lm + f;
   uint32_t fail = 0;
   const int m1 = min(m0 + kRowsPerWarp, c.M);
   for (int m = m0; m < m1; ++m) {
     const int d = c.deg(m);
-    if constexpr (FORM == 1) {
+    if constexpr (C8) {
       switch (d) {
-        case 6: fail |= f32s_check_ell<1, ES, 6, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm); break;
-        case 7: fail |= f32s_check_ell<1, ES, 7, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm); break;
-        case 14: fail |= f32s_check_ell<1, ES, 14, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm); break;
-        case 15: fail |= f32s_check_ell<1, ES, 15, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm); break;
-        default: fail |= f32s_check_ell<1, ES, 0, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm); break;
+        case 6: fail |= f32s_check_ell<1, ES, 6, WIDE, true>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
+        case 7: fail |= f32s_check_ell<1, ES, 7, WIDE, true>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
+        default: fail |= f32s_check_ell<1, ES, 0, WIDE, true>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
+      }
+    } else if constexpr (FORM == 1) {
+      switch (d) {
+        case 6: fail |= f32s_check_ell<1, ES, 6, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
+        case 7: fail |= f32s_check_ell<1, ES, 7, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
+        case 14: fail |= f32s_check_ell<1, ES, 14, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
+        case 15: fail |= f32s_check_ell<1, ES, 15, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
+        default: fail |= f32s_check_ell<1, ES, 0, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm); break;
       }
     } else {
-      if (d == 6) fail |= f32s_check_ell<0, ES, 6, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm);
-      else if (d == 7) fail |= f32s_check_ell<0, ES, 7, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm);
-      else fail |= f32s_check_ell<0, ES, 0, WIDE>(c, r, m, d, FL, Zp, Zn, St, Lm);
+      if (d == 6) fail |= f32s_check_ell<0, ES, 6, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm);
+      else if (d == 7) fail |= f32s_check_ell<0, ES, 7, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm);
+      else fail |= f32s_check_ell<0, ES, 0, WIDE>(c, r, m, d, FL, Zp, Zn, St, Sx, Lm);
     }
   }
   if (ES && fail) atomicOr(s.fail + cur * s.FL + f, 1u);
@@ -261,12 +282,9 @@ __device__ __forceinline__ uint32_t f32s_check_spa(const DevCode& c, int m, size
 
 template <bool ES>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_rows_spa(const DevCode c, F32S s, int k) {
-  const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FL / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
+  int chunk, m0;
+  if (!row_map<kChunksF32PE>(blockIdx.x, blockIdx.y, threadIdx.x >> 5, c.M, s.FL, chunk, m0)) return;
   const int f = chunk * 32 + lane;
   const int cur = k & 1;
   const bool active = s.act[cur * s.FL + f] != 0u;
@@ -313,10 +331,8 @@ __global__ void __launch_bounds__(256) f32s_cols(const DevCode c, F32S s, int k,
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_final_syndrome(const DevCode c, F32S s, int kf) {
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = s.FL / 32;
-  const int chunk = warp % n_chunks;
-  const int m0 = (warp / n_chunks) * kRowsPerWarp;
-  if (m0 >= c.M) return;
+  int chunk, m0;
+  if (!row_map_all(warp, c.M, s.FL, chunk, m0)) return;
   const int f = chunk * 32 + lane;
   const int cur = kf & 1;
   const bool active = s.act[cur * s.FL + f] != 0u;
@@ -383,12 +399,18 @@ __global__ void __launch_bounds__(256) f32s_output(const DevCode c, F32S s, int 
 template <int FORM, bool ES>
 cudaError_t f32s_run(const DevCode& c, const F32Rule& r, const StreamLayout& L, F32S s, int sm_count,
                      int32_t max_iter, cudaStream_t st) {
-  const int rgrid = rows_grid(c.M, L.lanes);
+  // row passes on 2-D grids of chunk groups (Section V form and per-edge form
+  // group sizes differ)
+  const RowGrid g2 = rows_grid_g(c.M, L.lanes, FORM == 1 ? kChunksSV : kChunksF32PE);
+  const dim3 rgrid((unsigned)g2.x, (unsigned)g2.y);
   const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
                    L.lanes / 32);
   const bool wide = c.ell16 == nullptr;
+  const bool c8 = c.ell_w <= 8;  // every check of degree <= 8: the 10-byte Section V state
   for (int k = 1; k <= max_iter; ++k) {
     if (FORM == 0 && r.rule == 3) f32s_rows_spa<ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, s, k);
+    else if (FORM == 1 && c8 && wide) f32s_rows_ell<1, ES, true, true><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
+    else if (FORM == 1 && c8) f32s_rows_ell<1, ES, false, true><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
     else if (wide) f32s_rows_ell<FORM, ES, true><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
     else f32s_rows_ell<FORM, ES, false><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
     f32s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k, k < max_iter ? 1 : 0);
