@@ -139,6 +139,8 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
                                                uint4* __restrict__ St, uint16_t* __restrict__ Lm) {
   constexpr int P = G / 2;
   constexpr int NJ = D > 0 ? D : DMAX;
+  // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
+  const uint32_t ksat = hfma(qm2, h2c_q11(16), h2c_q11(15));
   // one frame pair: the pass-1 handles stay in registers for pass 2; two pairs
   // need those registers for state and reload them
   constexpr bool KEEP = (P == 1 && FORM == 1 && !ES && ACC != 2);
@@ -167,8 +169,8 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
   uint32_t K1[P], K2[P], NEG[P], Y[P], SR[P], D2[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    K1[p] = h2c(2048);
-    K2[p] = h2c(2048);
+    K1[p] = ksat;  // the minima start at the saturated key, so they never exceed it
+    K2[p] = ksat;
     NEG[p] = 0;
     Y[p] = 0;
     if constexpr (FORM == 1) {
@@ -208,7 +210,12 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
         // added to NEG (the bits are disjoint), one multiply-add on the FMA pipe
         if (j == 0) NEG[p] = u & 0x80008000u;
         else NEG[p] = umad_hi(u & 0x80008000u, 1u << (32 - j), NEG[p]);
-        const uint32_t key = hfma(hmin(hab(u), qm2), h2c(16), h2c(j));
+        // key (16 |u| + j) 2^-11 clamped to 1 by one saturating multiply-add:
+        // exact for |u| <= 127 (16 |u| + j < 2048 fits 11 significand bits).
+        // Keys of |u| > Qm (Qm <= 127) exceed the minima's start (16 Qm + 15)
+        // 2^-11, so the minima come out as 16 min(|u|, Qm) + j; where both
+        // are saturated A = B and the position of the first does not matter
+        const uint32_t key = hfma_sat(hab(u), h2c_q11(16), h2c_q11(j));
         K2[p] = hmin(K2[p], hmax(K1[p], key));
         K1[p] = hmin(K1[p], key);
       }
@@ -226,8 +233,10 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
     const uint32_t pm = ((__popc(NEG[p] & 0xffffu) & 1) ? 0x0000ffffu : 0u) |
                         ((__popc(NEG[p] >> 16) & 1) ? 0xffff0000u : 0u);
     Sn[p] = (NEG[p] ^ pm) & (dlane | (dlane << 16));
-    const int32_t k1l = h_lo_int(K1[p]), k1h = h_hi_int(K1[p]);
-    const int32_t k2l = h_lo_int(K2[p]), k2h = h_hi_int(K2[p]);
+    // keys back to 16 min(|u|, Qm) + j (exact: a power of two)
+    const uint32_t k1 = hfma(K1[p], h2c(2048), 0u), k2 = hfma(K2[p], h2c(2048), 0u);
+    const int32_t k1l = h_lo_int(k1), k1h = h_hi_int(k1);
+    const int32_t k2l = h_lo_int(k2), k2h = h_hi_int(k2);
     const int32_t al = rule.g(k1l >> 4), ah = rule.g(k1h >> 4);
     const int32_t bl = rule.g(k2l >> 4), bh = rule.g(k2h >> 4);
     An[p] = small_to_h2(al, ah);

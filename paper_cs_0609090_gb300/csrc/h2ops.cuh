@@ -18,6 +18,9 @@ __host__ __device__ constexpr uint32_t hbits(int v) {
                              (e <= 10 ? ((v - (1 << e)) << (10 - e)) : ((v - (1 << e)) >> (e - 10))));
 }
 __host__ __device__ constexpr uint32_t h2c(int v) { return hbits(v) * 0x10001u; }
+// Pair of v 2^-11 for 0 <= v < 2048 (the exponent of v's pattern lowered by 11;
+// every such value is a normal binary16 number).
+__host__ __device__ constexpr uint32_t h2c_q11(int v) { return v == 0 ? 0u : (hbits(v) - (11u << 10)) * 0x10001u; }
 
 __device__ __forceinline__ uint32_t hadd(uint32_t a, uint32_t b) {
   uint32_t d; asm("add.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b)); return d;
@@ -30,6 +33,10 @@ __device__ __forceinline__ uint32_t hfma(uint32_t a, uint32_t b, uint32_t c) {
 }
 __device__ __forceinline__ uint32_t hfma_relu(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d; asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c)); return d;
+}
+// a b + c clamped to [0, 1].
+__device__ __forceinline__ uint32_t hfma_sat(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d; asm("fma.rn.sat.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c)); return d;
 }
 __device__ __forceinline__ uint32_t hmin(uint32_t a, uint32_t b) {
   uint32_t d; asm("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b)); return d;
