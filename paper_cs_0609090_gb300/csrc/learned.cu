@@ -33,12 +33,13 @@
 #include <cmath>
 
 #include "kernels.h"
+#include "stream_grid.h"
 
 namespace ldpc {
 namespace {
 
-constexpr int kLRows = 4;    // checks per warp task
-constexpr int kLWarps = 8;   // warps per block
+constexpr int kLRows = kRowsPerWarp;    // checks per warp task
+constexpr int kLWarps = kWarpsPerBlock;  // warps per block
 
 inline size_t lal(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -131,14 +132,14 @@ __global__ void __launch_bounds__(256) from_lanes(const float* __restrict__ src,
 }
 
 // Forward iteration k: Eq. (3) with the Section V state and beta[k][class].
+// One warp = kLRows checks for one chunk of 32 frames, chunk-major (a 2-D grid,
+// blockIdx.y = chunk): the checkpoint lines the warps in flight gather stay in L2.
 __global__ void __launch_bounds__(kLWarps * 32) lf_rows(const DevCode c, const uint8_t* __restrict__ rclass,
                                                         const float* __restrict__ beta, LView v, int k) {
-  const int warp = blockIdx.x * kLWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = v.FL / 32;
-  const int m0 = (warp / n_chunks) * kLRows;
-  if (m0 >= c.M) return;
-  const int f = (warp % n_chunks) * 32 + lane;
+  int chunk, m0;
+  if (!row_map<1>(blockIdx.x, blockIdx.y, threadIdx.x >> 5, c.M, v.FL, chunk, m0)) return;
+  const int f = chunk * 32 + lane;
   const size_t FL = (size_t)v.FL;
   const float* zp = v.z(k - 1);
   const uint4* sp = k > 1 ? v.s(k - 1) : nullptr;
@@ -202,18 +203,18 @@ __global__ void __launch_bounds__(kLWarps * 32) lb_rows(const DevCode c, const u
                                                         const float* __restrict__ dzk, const uint4* __restrict__ dun,
                                                         uint4* __restrict__ duc, float* __restrict__ dzp,
                                                         int F) {
-  const int warp = blockIdx.x * kLWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int n_chunks = v.FL / 32;
-  const int m0 = (warp / n_chunks) * kLRows;
-  if (m0 >= c.M) return;
-  const int f = (warp % n_chunks) * 32 + lane;
+  int chunk, m0;
+  if (!row_map<1>(blockIdx.x, blockIdx.y, threadIdx.x >> 5, c.M, v.FL, chunk, m0)) return;
+  const int f = chunk * 32 + lane;
+  // task = (chunk, check group): one row of partial offset gradients each
+  const size_t task = (size_t)chunk * ((c.M + kLRows - 1) / kLRows) + m0 / kLRows;
   const bool live = f < F;
   const size_t FL = (size_t)v.FL;
   const float* zp = v.z(k - 1);
   const uint4* sp = k > 1 ? v.s(k - 1) : nullptr;
   float gpart[4] = {0.f, 0.f, 0.f, 0.f};  // per class, up to 4 classes in registers
-  float* prow = v.part + (size_t)warp * v.C;
+  float* prow = v.part + task * v.C;
   const int m1 = min(m0 + kLRows, c.M);
   for (int m = m0; m < m1; ++m) {
     const int e0 = __ldg(c.rp + m), d = __ldg(c.rp + m + 1) - e0;
@@ -447,9 +448,9 @@ __global__ void __launch_bounds__(256) quantize_kernel(const float* __restrict__
   }
 }
 
-int rows_blocks(int M, int FL) {
-  const int64_t warps = (int64_t)((M + kLRows - 1) / kLRows) * (FL / 32);
-  return (int)((warps + kLWarps - 1) / kLWarps);
+dim3 rows_blocks(int M, int FL) {
+  const RowGrid g = rows_grid_g(M, FL, 1);
+  return dim3((unsigned)g.x, (unsigned)g.y);
 }
 
 }  // namespace
@@ -459,7 +460,7 @@ cudaError_t learned_forward(const DevCode& c, const uint8_t* rclass, int C, int 
   LView v = lview(ws, L, c.N, c.M, K, C);
   const dim3 tg((c.N + 63) / 64, L.FL / 32);
   to_lanes<<<tg, 256, 0, st>>>(llr, F, c.N, L.FL, v.z(0), v.acc);
-  const int rb = rows_blocks(c.M, L.FL);
+  const dim3 rb = rows_blocks(c.M, L.FL);
   const int cb = (int)std::min<size_t>(((size_t)c.N * L.FL + 255) / 256, 8192);
   for (int k = 1; k <= K; ++k) {
     lf_rows<<<rb, kLWarps * 32, 0, st>>>(c, rclass, beta, v, k);
@@ -487,7 +488,7 @@ cudaError_t learned_backward(const DevCode& c, const uint8_t* rclass, int C, int
     const dim3 tg((c.N + 63) / 64, L.FL / 32);
     to_lanes<<<tg, 256, 0, st>>>(dz_in, F, c.N, L.FL, v.dzb(K & 1), nullptr);
   }
-  const int rb = rows_blocks(c.M, L.FL);
+  const dim3 rb = rows_blocks(c.M, L.FL);
   const int zb = (int)std::min<size_t>((nfl + 255) / 256, 8192);
   for (int k = K; k >= 1; --k) {
     float* dzk = v.dzb(k & 1);
