@@ -9,6 +9,8 @@
 // Workspace (lane = frame, FL = frames padded to 32, index [.][FL] innermost):
 //   zck  (K+1) x [N][FL] f32   Z^(0) .. Z^(K) posteriors (checkpoints)
 //   sck   K    x [M][FL] uint4 Section V state after iteration k: {A, B, n~, signs}
+//                              (checks in the degree-sorted internal order, as
+//                              in du; their variables from the sorted table)
 //   acc   [N][FL] f32          accumulator of the forward
 //   dz    2 x [N][FL] f32      gradient w.r.t. Z^(k) (ping-pong)
 //   du    2 x [M][FL] uint4    per check: {n~, second-min position, dU at n~,
@@ -132,49 +134,102 @@ __global__ void __launch_bounds__(256) from_lanes(const float* __restrict__ src,
 }
 
 // Forward iteration k: Eq. (3) with the Section V state and beta[k][class].
-// One warp = kLRows checks for one chunk of 32 frames, chunk-major (a 2-D grid,
-// blockIdx.y = chunk): the checkpoint lines the warps in flight gather stay in L2.
-__global__ void __launch_bounds__(kLWarps * 32) lf_rows(const DevCode c, const uint8_t* __restrict__ rclass,
-                                                        const float* __restrict__ beta, LView v, int k) {
+// Degree class of internal check i: the checks are sorted by degree and the
+// classes are the distinct degrees in ascending order, so the class is the
+// index of the degree run the check falls in (at most 4 classes).
+__device__ __forceinline__ int check_class(const DevCode& c, int i) {
+  int r = 0;
+#pragma unroll
+  for (int q = 1; q < 4; ++q)
+    if (q < c.n_dc && i >= c.dc_end[q - 1]) r = q;
+  return r;
+}
+
+// Forward of internal check i for one frame (lane-offset pointers): Eq. (3)
+// with the Section V state and the offset bt, its variables from the
+// degree-sorted table (positions in row order).  D > 0: exactly D positions,
+// unrolled so that the check's loads are in flight together; D = 0: d.
+template <int D, bool WIDE>
+__device__ __forceinline__ void lf_check(const DevCode& c, int i, int d, float bt, size_t FL,
+                                         const float* __restrict__ zp, float* __restrict__ acc,
+                                         const uint4* __restrict__ sp, uint4* __restrict__ sn) {
+  const int M = c.M;
+  auto col = [&](int j) -> int {
+    return WIDE ? __ldg(c.ell32 + (size_t)j * M + i) : (int)__ldg(c.ell16 + (size_t)j * M + i);
+  };
+  float A = 0.f, B = 0.f;
+  int I = 0;
+  uint32_t S = 0;
+  if (sp != nullptr) {
+    const uint4 st = sp[(size_t)i * FL];
+    A = __uint_as_float(st.x); B = __uint_as_float(st.y); I = (int)st.z; S = st.w;
+  }
+  float mn1 = INFINITY, mn2 = INFINITY;
+  int idx = 0;
+  uint32_t neg = 0;
+  auto take = [&](int j, int n) {
+    const float z = zp[(size_t)n * FL];
+    const float mag = (j == I) ? B : A;
+    const float u = z - (((S >> j) & 1u) ? -mag : mag);
+    neg |= (u < 0.0f ? 1u : 0u) << j;
+    const float x = fabsf(u);
+    if (x < mn1) { mn2 = mn1; mn1 = x; idx = j; }
+    else if (x < mn2) { mn2 = x; }
+  };
+  constexpr int R = D > 0 ? D : 1;
+  int nn[R];
+  if constexpr (D > 0) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn[j] = col(j);
+#pragma unroll
+    for (int j = 0; j < D; ++j) take(j, nn[j]);
+  } else {
+    for (int j = 0; j < d; ++j) take(j, col(j));
+  }
+  const int dd = D > 0 ? D : d;
+  const uint32_t dm = dd >= 32 ? 0xffffffffu : ((1u << dd) - 1u);
+  const uint32_t Sn = ((__popc(neg) & 1) ? ~neg : neg) & dm;
+  const float An = fmaxf(mn1 - bt, 0.0f), Bn = fmaxf(mn2 - bt, 0.0f);
+  auto emit = [&](int j, int n) {
+    const float mag = (j == idx) ? Bn : An;
+    atomicAdd(acc + (size_t)n * FL, ((Sn >> j) & 1u) ? -mag : mag);
+  };
+  if constexpr (D > 0) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) emit(j, nn[j]);
+  } else {
+    for (int j = 0; j < d; ++j) emit(j, col(j));
+  }
+  sn[(size_t)i * FL] = make_uint4(__float_as_uint(An), __float_as_uint(Bn), (uint32_t)idx, Sn);
+}
+
+// Forward iteration k: Eq. (3) with the Section V state and beta[k][class].
+// One warp = kLRows internal checks for one chunk of 32 frames, chunk-major (a
+// 2-D grid, blockIdx.y = chunk): the checkpoint lines the warps in flight
+// gather stay in L2.
+template <bool WIDE>
+__global__ void __launch_bounds__(kLWarps * 32, 4) lf_rows(const DevCode c, const float* __restrict__ beta, LView v,
+                                                           int k) {
   const int lane = threadIdx.x & 31;
   int chunk, m0;
   if (!row_map<1>(blockIdx.x, blockIdx.y, threadIdx.x >> 5, c.M, v.FL, chunk, m0)) return;
   const int f = chunk * 32 + lane;
   const size_t FL = (size_t)v.FL;
-  const float* zp = v.z(k - 1);
-  const uint4* sp = k > 1 ? v.s(k - 1) : nullptr;
-  uint4* sn = v.s(k);
+  const float* zp = v.z(k - 1) + f;
+  float* acc = v.acc + f;
+  const uint4* sp = k > 1 ? v.s(k - 1) + f : nullptr;
+  uint4* sn = v.s(k) + f;
   const int m1 = min(m0 + kLRows, c.M);
-  for (int m = m0; m < m1; ++m) {
-    const int e0 = __ldg(c.rp + m), d = __ldg(c.rp + m + 1) - e0;
-    const float bt = __ldg(beta + (size_t)(k - 1) * v.C + rclass[m]);
-    float A = 0.f, B = 0.f;
-    int I = 0;
-    uint32_t S = 0;
-    if (sp != nullptr) {
-      const uint4 st = sp[(size_t)m * FL + f];
-      A = __uint_as_float(st.x); B = __uint_as_float(st.y); I = (int)st.z; S = st.w;
+  for (int i = m0; i < m1; ++i) {
+    const int d = c.deg(i);
+    const float bt = __ldg(beta + (size_t)(k - 1) * v.C + check_class(c, i));
+    switch (d) {
+      case 6: lf_check<6, WIDE>(c, i, d, bt, FL, zp, acc, sp, sn); break;
+      case 7: lf_check<7, WIDE>(c, i, d, bt, FL, zp, acc, sp, sn); break;
+      case 14: lf_check<14, WIDE>(c, i, d, bt, FL, zp, acc, sp, sn); break;
+      case 15: lf_check<15, WIDE>(c, i, d, bt, FL, zp, acc, sp, sn); break;
+      default: lf_check<0, WIDE>(c, i, d, bt, FL, zp, acc, sp, sn); break;
     }
-    float mn1 = INFINITY, mn2 = INFINITY;
-    int idx = 0;
-    uint32_t neg = 0;
-    for (int j = 0; j < d; ++j) {
-      const float z = zp[(size_t)__ldg(c.ci + e0 + j) * FL + f];
-      const float mag = (j == I) ? B : A;
-      const float u = z - (((S >> j) & 1u) ? -mag : mag);
-      neg |= (u < 0.0f ? 1u : 0u) << j;
-      const float a = fabsf(u);
-      if (a < mn1) { mn2 = mn1; mn1 = a; idx = j; }
-      else if (a < mn2) { mn2 = a; }
-    }
-    const uint32_t dm = d >= 32 ? 0xffffffffu : ((1u << d) - 1u);
-    const uint32_t Sn = ((__popc(neg) & 1) ? ~neg : neg) & dm;
-    const float An = fmaxf(mn1 - bt, 0.0f), Bn = fmaxf(mn2 - bt, 0.0f);
-    for (int j = 0; j < d; ++j) {
-      const float mag = (j == idx) ? Bn : An;
-      atomicAdd(v.acc + (size_t)__ldg(c.ci + e0 + j) * FL + f, ((Sn >> j) & 1u) ? -mag : mag);
-    }
-    sn[(size_t)m * FL + f] = make_uint4(__float_as_uint(An), __float_as_uint(Bn), (uint32_t)idx, Sn);
   }
 }
 
@@ -194,15 +249,86 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+// Backward of internal check i through iteration k for one frame (see the
+// file comment; lane-offset pointers).  Returns the check's dLoss/dbeta.
+template <int D, bool WIDE>
+__device__ __forceinline__ float lb_check(const DevCode& c, int i, int d, float bt, bool live, size_t FL,
+                                          const float* __restrict__ zp, const uint4* __restrict__ sp,
+                                          const float* __restrict__ dzk, const uint4* __restrict__ dun,
+                                          uint4* __restrict__ duc, float* __restrict__ dzp) {
+  const int M = c.M;
+  auto col = [&](int j) -> int {
+    return WIDE ? __ldg(c.ell32 + (size_t)j * M + i) : (int)__ldg(c.ell16 + (size_t)j * M + i);
+  };
+  float A = 0.f, B = 0.f;
+  int I = 0;
+  uint32_t S = 0;
+  if (sp != nullptr) {
+    const uint4 st = sp[(size_t)i * FL];
+    A = __uint_as_float(st.x); B = __uint_as_float(st.y); I = (int)st.z; S = st.w;
+  }
+  // recompute the forward row reduction
+  float mn1 = INFINITY, mn2 = INFINITY, u1 = 0.f, u2 = 0.f;
+  int a = 0, b = 1;
+  uint32_t neg = 0;
+  auto take = [&](int j, int n) {
+    const float z = zp[(size_t)n * FL];
+    const float mag = (j == I) ? B : A;
+    const float u = z - (((S >> j) & 1u) ? -mag : mag);
+    neg |= (u < 0.0f ? 1u : 0u) << j;
+    const float x = fabsf(u);
+    if (x < mn1) { mn2 = mn1; u2 = u1; b = a; mn1 = x; u1 = u; a = j; }
+    else if (x < mn2) { mn2 = x; u2 = u; b = j; }
+  };
+  constexpr int R = D > 0 ? D : 1;
+  int nn[R];
+  if constexpr (D > 0) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn[j] = col(j);
+#pragma unroll
+    for (int j = 0; j < D; ++j) take(j, nn[j]);
+  } else {
+    for (int j = 0; j < d; ++j) take(j, col(j));
+  }
+  const uint32_t sgnw = ((__popc(neg) & 1) ? ~neg : neg);  // bit j set: L^(k)_j negative
+  // sparse dLoss/du^(k+1) of this check
+  uint32_t na = 0xffffffffu, nb = 0xffffffffu;
+  float da = 0.f, db = 0.f;
+  if (dun != nullptr) {
+    const uint4 t = dun[(size_t)i * FL];
+    na = t.x; nb = t.y; da = __uint_as_float(t.z); db = __uint_as_float(t.w);
+  }
+  float dA = 0.f, dB = 0.f;
+  auto grad = [&](int j, int n) {
+    float G = dzk[(size_t)n * FL];
+    if ((uint32_t)j == na) G -= da;
+    if ((uint32_t)j == nb) G -= db;
+    const float sG = ((sgnw >> j) & 1u) ? -G : G;
+    if (j == a) dB += sG; else dA += sG;
+  };
+  // (the columns are loaded again rather than kept: keeping them spills at 4 CTAs
+  // per SM, and 3 CTAs per SM measured slower)
+#pragma unroll
+  for (int j = 0; j < (D > 0 ? D : d); ++j) grad(j, col(j));
+  const float gA = (mn1 > bt) ? dA : 0.0f;
+  const float gB = (mn2 > bt) ? dB : 0.0f;
+  const float dua = live ? gA * (u1 < 0.0f ? -1.0f : 1.0f) : 0.0f;
+  const float dub = live ? gB * (u2 < 0.0f ? -1.0f : 1.0f) : 0.0f;
+  duc[(size_t)i * FL] = make_uint4((uint32_t)a, (uint32_t)b, __float_as_uint(dua), __float_as_uint(dub));
+  if (dua != 0.0f) atomicAdd(dzp + (size_t)col(a) * FL, dua);
+  if (dub != 0.0f) atomicAdd(dzp + (size_t)col(b) * FL, dub);
+  return live ? -(gA + gB) : 0.0f;
+}
+
 // Backward through iteration k (see the file comment).  dzk: dLoss/dZ^(k);
 // dun: sparse dLoss/du^(k+1) of every check (nullptr when k == K); writes duc
 // (dLoss/du^(k)), adds into dzp (dLoss/dZ^(k-1)) and one partial dLoss/dbeta per
-// (task, class).
-__global__ void __launch_bounds__(kLWarps * 32) lb_rows(const DevCode c, const uint8_t* __restrict__ rclass,
-                                                        const float* __restrict__ beta, LView v, int k,
-                                                        const float* __restrict__ dzk, const uint4* __restrict__ dun,
-                                                        uint4* __restrict__ duc, float* __restrict__ dzp,
-                                                        int F) {
+// (task, class).  Same warp order and check bodies as the forward.
+template <bool WIDE>
+__global__ void __launch_bounds__(kLWarps * 32, 4) lb_rows(const DevCode c, const float* __restrict__ beta, LView v,
+                                                           int k, const float* __restrict__ dzk,
+                                                           const uint4* __restrict__ dun, uint4* __restrict__ duc,
+                                                           float* __restrict__ dzp, int F) {
   const int lane = threadIdx.x & 31;
   int chunk, m0;
   if (!row_map<1>(blockIdx.x, blockIdx.y, threadIdx.x >> 5, c.M, v.FL, chunk, m0)) return;
@@ -211,62 +337,30 @@ __global__ void __launch_bounds__(kLWarps * 32) lb_rows(const DevCode c, const u
   const size_t task = (size_t)chunk * ((c.M + kLRows - 1) / kLRows) + m0 / kLRows;
   const bool live = f < F;
   const size_t FL = (size_t)v.FL;
-  const float* zp = v.z(k - 1);
-  const uint4* sp = k > 1 ? v.s(k - 1) : nullptr;
+  const float* zp = v.z(k - 1) + f;
+  const uint4* sp = k > 1 ? v.s(k - 1) + f : nullptr;
+  dzk += f;
+  if (dun != nullptr) dun += f;
+  duc += f;
+  dzp += f;
   float gpart[4] = {0.f, 0.f, 0.f, 0.f};  // per class, up to 4 classes in registers
-  float* prow = v.part + task * v.C;
   const int m1 = min(m0 + kLRows, c.M);
-  for (int m = m0; m < m1; ++m) {
-    const int e0 = __ldg(c.rp + m), d = __ldg(c.rp + m + 1) - e0;
-    const int cls = rclass[m];
+  for (int i = m0; i < m1; ++i) {
+    const int d = c.deg(i);
+    const int cls = check_class(c, i);
     const float bt = __ldg(beta + (size_t)(k - 1) * v.C + cls);
-    float A = 0.f, B = 0.f;
-    int I = 0;
-    uint32_t S = 0;
-    if (sp != nullptr) {
-      const uint4 st = sp[(size_t)m * FL + f];
-      A = __uint_as_float(st.x); B = __uint_as_float(st.y); I = (int)st.z; S = st.w;
+    float g;
+    switch (d) {
+      case 6: g = lb_check<6, WIDE>(c, i, d, bt, live, FL, zp, sp, dzk, dun, duc, dzp); break;
+      case 7: g = lb_check<7, WIDE>(c, i, d, bt, live, FL, zp, sp, dzk, dun, duc, dzp); break;
+      case 14: g = lb_check<14, WIDE>(c, i, d, bt, live, FL, zp, sp, dzk, dun, duc, dzp); break;
+      case 15: g = lb_check<15, WIDE>(c, i, d, bt, live, FL, zp, sp, dzk, dun, duc, dzp); break;
+      default: g = lb_check<0, WIDE>(c, i, d, bt, live, FL, zp, sp, dzk, dun, duc, dzp); break;
     }
-    // recompute the forward row reduction
-    float mn1 = INFINITY, mn2 = INFINITY, u1 = 0.f, u2 = 0.f;
-    int a = 0, b = 1;
-    uint32_t neg = 0;
-    for (int j = 0; j < d; ++j) {
-      const float z = zp[(size_t)__ldg(c.ci + e0 + j) * FL + f];
-      const float mag = (j == I) ? B : A;
-      const float u = z - (((S >> j) & 1u) ? -mag : mag);
-      neg |= (u < 0.0f ? 1u : 0u) << j;
-      const float x = fabsf(u);
-      if (x < mn1) { mn2 = mn1; u2 = u1; b = a; mn1 = x; u1 = u; a = j; }
-      else if (x < mn2) { mn2 = x; u2 = u; b = j; }
-    }
-    const uint32_t sgnw = ((__popc(neg) & 1) ? ~neg : neg);  // bit j set: L^(k)_j negative
-    // sparse dLoss/du^(k+1) of this check
-    uint32_t na = 0xffffffffu, nb = 0xffffffffu;
-    float da = 0.f, db = 0.f;
-    if (dun != nullptr) {
-      const uint4 t = dun[(size_t)m * FL + f];
-      na = t.x; nb = t.y; da = __uint_as_float(t.z); db = __uint_as_float(t.w);
-    }
-    float dA = 0.f, dB = 0.f;
-    for (int j = 0; j < d; ++j) {
-      float G = dzk[(size_t)__ldg(c.ci + e0 + j) * FL + f];
-      if ((uint32_t)j == na) G -= da;
-      if ((uint32_t)j == nb) G -= db;
-      const float sG = ((sgnw >> j) & 1u) ? -G : G;
-      if (j == a) dB += sG; else dA += sG;
-    }
-    const float gA = (mn1 > bt) ? dA : 0.0f;
-    const float gB = (mn2 > bt) ? dB : 0.0f;
-    const float gbeta = live ? -(gA + gB) : 0.0f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) gpart[q] += (cls == q) ? gbeta : 0.0f;
-    const float dua = live ? gA * (u1 < 0.0f ? -1.0f : 1.0f) : 0.0f;
-    const float dub = live ? gB * (u2 < 0.0f ? -1.0f : 1.0f) : 0.0f;
-    duc[(size_t)m * FL + f] = make_uint4((uint32_t)a, (uint32_t)b, __float_as_uint(dua), __float_as_uint(dub));
-    if (dua != 0.0f) atomicAdd(dzp + (size_t)__ldg(c.ci + e0 + a) * FL + f, dua);
-    if (dub != 0.0f) atomicAdd(dzp + (size_t)__ldg(c.ci + e0 + b) * FL + f, dub);
+    for (int q = 0; q < 4; ++q) gpart[q] += (cls == q) ? g : 0.0f;
   }
+  float* prow = v.part + task * v.C;
   for (int q = 0; q < v.C && q < 4; ++q) {
     const float s = warp_sum(gpart[q]);
     if (lane == 0) prow[q] = s;
@@ -457,13 +551,16 @@ dim3 rows_blocks(int M, int FL) {
 
 cudaError_t learned_forward(const DevCode& c, const uint8_t* rclass, int C, int K, const float* beta,
                             const LearnedLayout& L, void* ws, const float* llr, int F, float* zout, cudaStream_t st) {
+  (void)rclass;  // the row kernels take a check's class from its degree run in the sorted order
   LView v = lview(ws, L, c.N, c.M, K, C);
   const dim3 tg((c.N + 63) / 64, L.FL / 32);
   to_lanes<<<tg, 256, 0, st>>>(llr, F, c.N, L.FL, v.z(0), v.acc);
   const dim3 rb = rows_blocks(c.M, L.FL);
   const int cb = (int)std::min<size_t>(((size_t)c.N * L.FL + 255) / 256, 8192);
+  const bool wide = c.ell16 == nullptr;
   for (int k = 1; k <= K; ++k) {
-    lf_rows<<<rb, kLWarps * 32, 0, st>>>(c, rclass, beta, v, k);
+    if (wide) lf_rows<true><<<rb, kLWarps * 32, 0, st>>>(c, beta, v, k);
+    else lf_rows<false><<<rb, kLWarps * 32, 0, st>>>(c, beta, v, k);
     lf_cols<<<cb, 256, 0, st>>>(v, k);
   }
   if (zout != nullptr) from_lanes<<<tg, 256, 0, st>>>(v.z(K), F, c.N, L.FL, zout);
@@ -482,6 +579,7 @@ cudaError_t learned_bce(const DevCode& c, int C, int K, const LearnedLayout& L, 
 cudaError_t learned_backward(const DevCode& c, const uint8_t* rclass, int C, int K, const float* beta,
                              const LearnedLayout& L, void* ws, const float* dz_in, int F, float* dbeta,
                              cudaStream_t st) {
+  (void)rclass;  // the row kernels take a check's class from its degree run in the sorted order
   LView v = lview(ws, L, c.N, c.M, K, C);
   const size_t nfl = (size_t)c.N * L.FL;
   if (dz_in != nullptr) {
@@ -496,7 +594,8 @@ cudaError_t learned_backward(const DevCode& c, const uint8_t* rclass, int C, int
     zero_f<<<zb, 256, 0, st>>>(dzp, nfl);
     const uint4* dun = (k == K) ? nullptr : v.dub((k + 1) & 1);
     uint4* duc = v.dub(k & 1);
-    lb_rows<<<rb, kLWarps * 32, 0, st>>>(c, rclass, beta, v, k, dzk, dun, duc, dzp, F);
+    if (c.ell16 == nullptr) lb_rows<true><<<rb, kLWarps * 32, 0, st>>>(c, beta, v, k, dzk, dun, duc, dzp, F);
+    else lb_rows<false><<<rb, kLWarps * 32, 0, st>>>(c, beta, v, k, dzk, dun, duc, dzp, F);
     // stage partials in the loss-partials buffer (4096 floats >= kReduceBlocks * C)
     lb_reduce1<<<kReduceBlocks, 256, 0, st>>>(v.part, L.tasks, C, v.lpart);
     lb_reduce2<<<1, 256, 0, st>>>(v.lpart, kReduceBlocks, C, dbeta + (size_t)(k - 1) * C);
