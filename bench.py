@@ -210,7 +210,8 @@ def cpu_oracle_sample(w, form: str, budget_s: float, max_frames: int, layers=Non
     chunk = max(oracle.default_threads() * 2, 8)
     done, t_total = 0, 0.0
     kw = dict(rule=p["rule"], offset=p.get("offset", 0), norm_num=p.get("norm_num", 3),
-              norm_shift=p.get("norm_shift", 2), msg_sat=p["msg_sat"], max_iter=p["max_iter"], early_stop=0)
+              norm_shift=p.get("norm_shift", 2), msg_sat=p["msg_sat"], max_iter=p["max_iter"],
+              early_stop=p.get("early_stop", 0))
     while done < max_frames and t_total < budget_s:
         q = w.q0[done % w.n_frames:][:chunk]
         t0 = time.perf_counter()
@@ -223,7 +224,7 @@ def cpu_oracle_sample(w, form: str, budget_s: float, max_frames: int, layers=Non
     gbps = done * w.K / t_total / 1e9
     return dict(value=gbps, unit=UNIT, cores=oracle.default_threads(), kind="oracle",
                 sample=f"{done} of {w.n_frames} frames of {w.name}, {p['max_iter']} iterations, "
-                       f"early stop off, {form}, {t_total:.1f} s"), t_total / done
+                       f"early stop {'on' if p.get('early_stop', 0) else 'off'}, {form}, {t_total:.1f} s"), t_total / done
 
 
 def dist_setup(args):
@@ -604,6 +605,11 @@ def main():
                     help="decode this many frames of the workload instead of its batch (profiling runs)")
     ap.add_argument("--iters", type=int, default=None,
                     help="run this many iterations instead of the workload's (profiling runs)")
+    ap.add_argument("--ebn0", type=float, default=None,
+                    help="channel Eb/N0 in dB instead of the workload's (analysis runs)")
+    ap.add_argument("--early-stop", action="store_true",
+                    help="stop each frame at a codeword (analysis runs; the metric is quoted at fixed "
+                         "iterations, so the line then reports the mean iterations too)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -620,8 +626,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = I.make_workload(args.workload, frame_seed=1 + rank, n_frames=args.frames)
-    w.params["early_stop"] = 0
+    w = I.make_workload(args.workload, frame_seed=1 + rank, n_frames=args.frames, ebn0_db=args.ebn0)
+    w.params["early_stop"] = 1 if args.early_stop else 0
     if args.iters is not None:
         w.params["max_iter"] = args.iters
     F, N, K = w.n_frames, w.code.n_vars, w.K
@@ -666,7 +672,9 @@ def main():
             step()
     torch.cuda.synchronize()
     # all frames ran the fixed iteration count
-    assert int(iters.min()) == w.params["max_iter"] and int(iters.max()) == w.params["max_iter"]
+    if not args.early_stop:
+        assert int(iters.min()) == w.params["max_iter"] and int(iters.max()) == w.params["max_iter"]
+    mean_iters = float(iters.double().mean().item())
 
     if world > 1:
         import torch.distributed as dist
@@ -749,7 +757,8 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     e2e_ms = t0.elapsed_time(t1)
-    assert int(h_iters.min()) == w.params["max_iter"] and int(h_iters.max()) == w.params["max_iter"]
+    if not args.early_stop:
+        assert int(h_iters.min()) == w.params["max_iter"] and int(h_iters.max()) == w.params["max_iter"]
 
     if world > 1:
         import torch.distributed as dist
@@ -776,7 +785,8 @@ def main():
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": w.name, "form": args.form, "n_frames": F, "iters": w.params["max_iter"],
                        "N": N, "M": w.code.n_checks, "E": w.code.n_edges, "K": K,
-                       "ebn0_db": w.ebn0_db, "rule": w.params["rule"], "early_stop": 0,
+                       "ebn0_db": w.ebn0_db, "rule": w.params["rule"], "early_stop": w.params["early_stop"],
+                       "mean_iters": mean_iters,
                        "l2": "flushed between timed steps (256 MB write)", "frames_per_rank": F,
                        "kernel": args.kernel, "schedule": args.schedule},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(host_llr.nbytes),

@@ -11,7 +11,8 @@
 //   sck   K    x [M][FL] uint4 Section V state after iteration k: {A, B, n~, signs}
 //                              (checks in the degree-sorted internal order, as
 //                              in du; their variables from the sorted table)
-//   acc   [N][FL] f32          accumulator of the forward
+//   (no accumulator: the forward's row pass of iteration k adds its messages
+//    into zck[k], which holds Z^(0) beforehand, so that it ends as Z^(k))
 //   dz    2 x [N][FL] f32      gradient w.r.t. Z^(k) (ping-pong)
 //   du    2 x [M][FL] uint4    per check: {n~, second-min position, dU at n~,
 //                              dU at second} -- the only nonzero entries of
@@ -55,7 +56,7 @@ LearnedLayout learned_layout(int N, int M, int K, int C, int F) {
   size_t off = 0;
   L.zck = off;   off = lal(off + (size_t)(K + 1) * N * FL * 4);
   L.sck = off;   off = lal(off + (size_t)std::max(K, 1) * M * FL * 16);
-  L.acc = off;   off = lal(off + (size_t)N * FL * 4);
+  L.acc = off;   // unused: the forward accumulates into the checkpoints
   L.dz = off;    off = lal(off + 2 * (size_t)N * FL * 4);
   L.du = off;    off = lal(off + 2 * (size_t)M * FL * 16);
   L.part = off;  off = lal(off + (size_t)L.tasks * C * 4);
@@ -70,7 +71,6 @@ struct LView {
   int N, M, K, C, FL;
   float* zck;
   uint4* sck;
-  float* acc;
   float* dz;
   uint4* du;
   float* part;
@@ -87,7 +87,6 @@ LView lview(void* ws, const LearnedLayout& L, int N, int M, int K, int C) {
   v.N = N; v.M = M; v.K = K; v.C = C; v.FL = L.FL;
   v.zck = reinterpret_cast<float*>(b + L.zck);
   v.sck = reinterpret_cast<uint4*>(b + L.sck);
-  v.acc = reinterpret_cast<float*>(b + L.acc);
   v.dz = reinterpret_cast<float*>(b + L.dz);
   v.du = reinterpret_cast<uint4*>(b + L.du);
   v.part = reinterpret_cast<float*>(b + L.part);
@@ -216,7 +215,7 @@ __global__ void __launch_bounds__(kLWarps * 32, 4) lf_rows(const DevCode c, cons
   const int f = chunk * 32 + lane;
   const size_t FL = (size_t)v.FL;
   const float* zp = v.z(k - 1) + f;
-  float* acc = v.acc + f;
+  float* acc = v.z(k) + f;  // holds Z^(0); Z^(k) after the pass
   const uint4* sp = k > 1 ? v.s(k - 1) + f : nullptr;
   uint4* sn = v.s(k) + f;
   const int m1 = min(m0 + kLRows, c.M);
@@ -233,15 +232,13 @@ __global__ void __launch_bounds__(kLWarps * 32, 4) lf_rows(const DevCode c, cons
   }
 }
 
-// Z^(k) = acc; acc = Z^(0) for the next iteration.
-__global__ void __launch_bounds__(256) lf_cols(LView v, int k) {
+// Z^(0) into checkpoint k, where the row pass of iteration k accumulates Z^(k).
+__global__ void __launch_bounds__(256) lf_init(LView v, int k) {
   const size_t total = (size_t)v.N * v.FL;
-  float* zk = v.z(k);
-  const float* z0 = v.z(0);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    zk[i] = v.acc[i];
-    v.acc[i] = z0[i];
-  }
+  float4* zk = reinterpret_cast<float4*>(v.z(k));
+  const float4* z0 = reinterpret_cast<const float4*>(v.z(0));
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total / 4; i += (size_t)gridDim.x * blockDim.x)
+    zk[i] = z0[i];
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -554,14 +551,14 @@ cudaError_t learned_forward(const DevCode& c, const uint8_t* rclass, int C, int 
   (void)rclass;  // the row kernels take a check's class from its degree run in the sorted order
   LView v = lview(ws, L, c.N, c.M, K, C);
   const dim3 tg((c.N + 63) / 64, L.FL / 32);
-  to_lanes<<<tg, 256, 0, st>>>(llr, F, c.N, L.FL, v.z(0), v.acc);
+  to_lanes<<<tg, 256, 0, st>>>(llr, F, c.N, L.FL, v.z(0), K >= 1 ? v.z(1) : nullptr);
   const dim3 rb = rows_blocks(c.M, L.FL);
   const int cb = (int)std::min<size_t>(((size_t)c.N * L.FL + 255) / 256, 8192);
   const bool wide = c.ell16 == nullptr;
   for (int k = 1; k <= K; ++k) {
     if (wide) lf_rows<true><<<rb, kLWarps * 32, 0, st>>>(c, beta, v, k);
     else lf_rows<false><<<rb, kLWarps * 32, 0, st>>>(c, beta, v, k);
-    lf_cols<<<cb, 256, 0, st>>>(v, k);
+    if (k < K) lf_init<<<cb, 256, 0, st>>>(v, k + 1);
   }
   if (zout != nullptr) from_lanes<<<tg, 256, 0, st>>>(v.z(K), F, c.N, L.FL, zout);
   return cudaGetLastError();
