@@ -34,7 +34,6 @@ struct ldpc_code {
   uint8_t* d_rdeg = nullptr;
   int32_t* d_cptr = nullptr;
   int32_t* d_cslot = nullptr;
-  uint8_t* d_rclass = nullptr;      // degree class of every check
   int32_t n_classes = 0;
   int32_t class_deg[32] = {};       // check degree of each class, ascending
   int32_t ell_w = 0;

@@ -126,16 +126,17 @@ cudaError_t stream_f32_decode(const DevCode& c, const F32Rule& r, int form, cons
 // Learned offsets beta[k][class]: workspace layout and launchers (learned.cu).
 struct LearnedLayout {
   int FL = 0, tasks = 0;
-  size_t zck = 0, sck = 0, acc = 0, dz = 0, du = 0, part = 0, lpart = 0, total = 0;
+  size_t zck = 0, sck = 0, dz = 0, du = 0, part = 0, lpart = 0, total = 0;
 };
 LearnedLayout learned_layout(int N, int M, int K, int C, int F);
-cudaError_t learned_forward(const DevCode& c, const uint8_t* rclass, int C, int K, const float* beta,
-                            const LearnedLayout& L, void* ws, const float* llr, int F, float* zout, cudaStream_t st);
+// A check's degree class is the index of its degree run in the internal
+// (degree-sorted) order: the classes are the distinct degrees, ascending.
+cudaError_t learned_forward(const DevCode& c, int C, int K, const float* beta, const LearnedLayout& L, void* ws,
+                            const float* llr, int F, float* zout, cudaStream_t st);
 cudaError_t learned_bce(const DevCode& c, int C, int K, const LearnedLayout& L, void* ws, int F,
                         const uint8_t* tbits, float* loss, bool want_grad, cudaStream_t st);
-cudaError_t learned_backward(const DevCode& c, const uint8_t* rclass, int C, int K, const float* beta,
-                             const LearnedLayout& L, void* ws, const float* dz_in, int F, float* dbeta,
-                             cudaStream_t st);
+cudaError_t learned_backward(const DevCode& c, int C, int K, const float* beta, const LearnedLayout& L, void* ws,
+                             const float* dz_in, int F, float* dbeta, cudaStream_t st);
 cudaError_t adam_step(float* p, const float* g, float* m, float* v, int n, int step, float lr, float b1, float b2,
                       float eps, cudaStream_t st);
 cudaError_t awgn_llr(int N, uint64_t seed, uint64_t first_frame, int F, float lo, float hi, float rate,

@@ -287,10 +287,6 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   for (int32_t dgr = 2; dgr <= 32; ++dgr)
     for (int32_t m = 0; m < n_checks; ++m)
       if (row_ptr[m + 1] - row_ptr[m] == dgr) { cls_deg[n_cls++] = dgr; break; }
-  std::vector<uint8_t> rclass((size_t)n_checks);
-  for (int32_t m = 0; m < n_checks; ++m)
-    for (int32_t q = 0; q < n_cls; ++q)
-      if (cls_deg[q] == row_ptr[m + 1] - row_ptr[m]) rclass[(size_t)m] = (uint8_t)q;
   // The frame-resident kernels visit checks in an internal order sorted by degree
   // (stable), so that the checks of a warp share one degree; check order does not
   // change any result (each check's messages depend only on the previous
@@ -364,8 +360,6 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
       (err = cudaMalloc(&c->d_cslot, sizeof(int32_t) * (size_t)E)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_cslot, cslot.data(), sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
-      (err = cudaMalloc(&c->d_rclass, (size_t)n_checks)) != cudaSuccess ||
-      (err = cudaMemcpy(c->d_rclass, rclass.data(), (size_t)n_checks, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMalloc(&c->d_rdeg, (size_t)n_checks)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_rdeg, rdeg.data(), (size_t)n_checks, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (narrow && (err = cudaMalloc(&c->d_ell16, sizeof(uint16_t) * ell16.size())) != cudaSuccess) ||
@@ -385,7 +379,6 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
     cudaFree(c->d_ell32);
     cudaFree(c->d_cptr);
     cudaFree(c->d_cslot);
-    cudaFree(c->d_rclass);
     delete c;
     return cuda_fail(err, "ldpc_code_create device copy");
   }
@@ -436,7 +429,6 @@ ldpc_status ldpc_code_destroy(ldpc_code* code) {
   cudaFree(code->d_ell32);
   cudaFree(code->d_cptr);
   cudaFree(code->d_cslot);
-  cudaFree(code->d_rclass);
   cudaFree(code->d_lay_ptr);
   cudaFree(code->d_lay_rows);
   free_cluster_tables(code);
@@ -605,7 +597,7 @@ ldpc_status ldpc_learned_forward(const ldpc_code* code, int32_t n_iters, const f
   if (s != LDPC_OK) return s;
   if (beta == nullptr || llr == nullptr) return fail(LDPC_ERR_INVALID_ARG, "beta and llr must be non-NULL");
   DeviceGuard guard(code->device);
-  const cudaError_t e = ldpc::learned_forward(view(code), code->d_rclass, code->n_classes, n_iters, beta, L,
+  const cudaError_t e = ldpc::learned_forward(view(code), code->n_classes, n_iters, beta, L,
                                               workspace, llr, n_frames, z_out, (cudaStream_t)stream);
   return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_learned_forward launch");
 }
@@ -631,7 +623,7 @@ ldpc_status ldpc_learned_backward(const ldpc_code* code, int32_t n_iters, const 
   if (s != LDPC_OK) return s;
   if (beta == nullptr || dbeta == nullptr) return fail(LDPC_ERR_INVALID_ARG, "beta and dbeta must be non-NULL");
   DeviceGuard guard(code->device);
-  const cudaError_t e = ldpc::learned_backward(view(code), code->d_rclass, code->n_classes, n_iters, beta, L,
+  const cudaError_t e = ldpc::learned_backward(view(code), code->n_classes, n_iters, beta, L,
                                                workspace, dz, n_frames, dbeta, (cudaStream_t)stream);
   return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_learned_backward launch");
 }

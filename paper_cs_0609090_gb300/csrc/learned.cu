@@ -56,7 +56,6 @@ LearnedLayout learned_layout(int N, int M, int K, int C, int F) {
   size_t off = 0;
   L.zck = off;   off = lal(off + (size_t)(K + 1) * N * FL * 4);
   L.sck = off;   off = lal(off + (size_t)std::max(K, 1) * M * FL * 16);
-  L.acc = off;   // unused: the forward accumulates into the checkpoints
   L.dz = off;    off = lal(off + 2 * (size_t)N * FL * 4);
   L.du = off;    off = lal(off + 2 * (size_t)M * FL * 16);
   L.part = off;  off = lal(off + (size_t)L.tasks * C * 4);
@@ -546,9 +545,8 @@ dim3 rows_blocks(int M, int FL) {
 
 }  // namespace
 
-cudaError_t learned_forward(const DevCode& c, const uint8_t* rclass, int C, int K, const float* beta,
-                            const LearnedLayout& L, void* ws, const float* llr, int F, float* zout, cudaStream_t st) {
-  (void)rclass;  // the row kernels take a check's class from its degree run in the sorted order
+cudaError_t learned_forward(const DevCode& c, int C, int K, const float* beta, const LearnedLayout& L, void* ws,
+                            const float* llr, int F, float* zout, cudaStream_t st) {
   LView v = lview(ws, L, c.N, c.M, K, C);
   const dim3 tg((c.N + 63) / 64, L.FL / 32);
   to_lanes<<<tg, 256, 0, st>>>(llr, F, c.N, L.FL, v.z(0), K >= 1 ? v.z(1) : nullptr);
@@ -573,10 +571,8 @@ cudaError_t learned_bce(const DevCode& c, int C, int K, const LearnedLayout& L, 
   return cudaGetLastError();
 }
 
-cudaError_t learned_backward(const DevCode& c, const uint8_t* rclass, int C, int K, const float* beta,
-                             const LearnedLayout& L, void* ws, const float* dz_in, int F, float* dbeta,
-                             cudaStream_t st) {
-  (void)rclass;  // the row kernels take a check's class from its degree run in the sorted order
+cudaError_t learned_backward(const DevCode& c, int C, int K, const float* beta, const LearnedLayout& L, void* ws,
+                             const float* dz_in, int F, float* dbeta, cudaStream_t st) {
   LView v = lview(ws, L, c.N, c.M, K, C);
   const size_t nfl = (size_t)c.N * L.FL;
   if (dz_in != nullptr) {

@@ -298,9 +298,64 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB) h2s_rows_ell(const 
   if (ES && fail) atomicOr(s.fail + cur * s.FP + p, fail);
 }
 
-// Stop rule and accumulator reset for every (variable, pair); pair-level flags
-// are advanced by the threads of variable 0.
-template <bool ES, bool DELTA>
+// The column pass of the delta form with four frame pairs per thread: 16-byte
+// accesses (a warp moves 512 bytes per variable), so that the pass streams at
+// copy speed; the frames that continue take Z^(k), the others keep theirs.
+// Pair-level flags are advanced by the threads of the first variable slice.
+// The frame-pair count is a multiple of 32, so groups of 4 pairs never
+// straddle it.
+template <bool ES>
+__global__ void __launch_bounds__(256) h2s_cols4(const DevCode c, H2S s, int k) {
+  const int p0 = (blockIdx.y * 32 + (threadIdx.x & 31)) * 4;
+  if (p0 >= s.FP) return;
+  const int cur = k & 1, nxt = cur ^ 1;
+  const uint4 act = *reinterpret_cast<const uint4*>(s.act + cur * s.FP + p0);
+  uint4 fail = make_uint4(0u, 0u, 0u, 0u);
+  if (ES) fail = *reinterpret_cast<const uint4*>(s.fail + cur * s.FP + p0);
+  const uint4 stop = ES ? make_uint4(act.x & ~fail.x, act.y & ~fail.y, act.z & ~fail.z, act.w & ~fail.w)
+                        : make_uint4(0u, 0u, 0u, 0u);
+  const uint4 cont = make_uint4(act.x & ~stop.x, act.y & ~stop.y, act.z & ~stop.z, act.w & ~stop.w);
+  auto selm = [](uint32_t cn) { return ((cn & 1u) ? 0x0000ffffu : 0u) | ((cn & 2u) ? 0xffff0000u : 0u); };
+  const uint4 sel = make_uint4(selm(cont.x), selm(cont.y), selm(cont.z), selm(cont.w));
+  const bool all = (sel.x & sel.y & sel.z & sel.w) == 0xffffffffu;
+  const bool any = (cont.x | cont.y | cont.z | cont.w) != 0u;
+  auto conv = [](uint32_t a) {
+    const uint32_t zz = acc_to_pair((int32_t)a);
+    return ints_to_h2(lo16(zz), hi16(zz));
+  };
+  if (any) {
+#pragma unroll 4
+    for (int n = blockIdx.x * 8 + (threadIdx.x >> 5); n < c.N; n += gridDim.x * 8) {
+      const size_t o = (size_t)n * s.FP + p0;
+      const uint4 a = *reinterpret_cast<const uint4*>(s.acc + o);
+      uint4 h = make_uint4(conv(a.x), conv(a.y), conv(a.z), conv(a.w));
+      if (!all) {
+        const uint4 z = *reinterpret_cast<const uint4*>(s.z + o);
+        h = make_uint4((h.x & sel.x) | (z.x & ~sel.x), (h.y & sel.y) | (z.y & ~sel.y),
+                       (h.z & sel.z) | (z.z & ~sel.z), (h.w & sel.w) | (z.w & ~sel.w));
+      }
+      *reinterpret_cast<uint4*>(s.z + o) = h;
+    }
+  }
+  if (blockIdx.x == 0) {
+    *reinterpret_cast<uint4*>(s.act + nxt * s.FP + p0) = cont;
+    *reinterpret_cast<uint4*>(s.fail + nxt * s.FP + p0) = make_uint4(0u, 0u, 0u, 0u);
+    if (ES) {
+      const uint32_t st[4] = {stop.x, stop.y, stop.z, stop.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (st[q] & 1u) s.iters[2 * (p0 + q)] = k - 1;
+        if (st[q] & 2u) s.iters[2 * (p0 + q) + 1] = k - 1;
+        s.ok[p0 + q] |= st[q];
+      }
+    }
+  }
+}
+
+// The column pass of the CSR kernel's resetting form: stop rule, Z^(k) for the
+// frames that continue, accumulator reset to Z0 for every (variable, pair);
+// pair-level flags are advanced by the threads of variable 0.
+template <bool ES>
 __global__ void __launch_bounds__(256) h2s_cols(const DevCode c, H2S s, int k) {
   const int p = blockIdx.y * 32 + (threadIdx.x & 31);
   const int cur = k & 1, nxt = cur ^ 1;
@@ -312,16 +367,10 @@ __global__ void __launch_bounds__(256) h2s_cols(const DevCode c, H2S s, int k) {
     const size_t o = (size_t)n * s.FP + p;
     const uint32_t zz = acc_to_pair(s.acc[o]);
     const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
-    if constexpr (DELTA) {
-      // the accumulator carries on; only the frames that continue take Z^(k)
-      if (cont == 3u) s.z[o] = h;
-      else if (cont != 0u) s.z[o] = (h & sel) | (s.z[o] & ~sel);
-    } else {
-      s.z[o] = (h & sel) | (s.z[o] & ~sel);
-      const uint32_t q = s.q0[o];
-      s.acc[o] = (int32_t)((uint32_t)acc_pack((int32_t)(int8_t)(q & 0xffu), (int32_t)(int8_t)(q >> 8)) -
-                           (uint32_t)__ldg(c.cdeg + n) * 0x66006600u);
-    }
+    s.z[o] = (h & sel) | (s.z[o] & ~sel);
+    const uint32_t q = s.q0[o];
+    s.acc[o] = (int32_t)((uint32_t)acc_pack((int32_t)(int8_t)(q & 0xffu), (int32_t)(int8_t)(q >> 8)) -
+                         (uint32_t)__ldg(c.cdeg + n) * 0x66006600u);
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {
     s.act[nxt * s.FP + p] = cont;
@@ -417,6 +466,8 @@ cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H
   const dim3 egrid = FORM == 1 ? dim3((unsigned)g2.x, (unsigned)g2.y) : dim3((unsigned)rgrid);
   const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
                    L.lanes / 32);
+  const int gy4 = (L.lanes / 4 + 31) / 32;  // groups of 32 threads x 4 pairs
+  const dim3 cgrid4((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / gy4)), (unsigned)gy4);
   const bool wide = c.ell16 == nullptr;
   const bool c8 = c.ell_w <= 8;  // every check of degree <= 8: the 8-byte Section V state
   for (int k = 1; k <= max_iter; ++k) {
@@ -426,10 +477,10 @@ cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H
         else h2s_rows_ell<1, ES, false, 4, true, true><<<egrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
       } else if (wide) h2s_rows_ell<FORM, ES, true, 4, true><<<egrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
       else h2s_rows_ell<FORM, ES, false, 4, true><<<egrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
-      h2s_cols<ES, true><<<cgrid, 256, 0, st>>>(c, s, k);
+      h2s_cols4<ES><<<cgrid4, 256, 0, st>>>(c, s, k);
     } else {
       h2s_rows<FORM, ES><<<rgrid, kWarpsPerBlock * 32, 0, st>>>(c, r, s, k);
-      h2s_cols<ES, false><<<cgrid, 256, 0, st>>>(c, s, k);
+      h2s_cols<ES><<<cgrid, 256, 0, st>>>(c, s, k);
     }
   }
   return cudaGetLastError();

@@ -303,27 +303,52 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) f32s_rows_spa(const DevCo
 // Column pass of iteration k: a frame whose Z^(k-1) satisfied every check
 // (seen by the row pass) stops at k - 1 with its result in zb(k - 1); a frame
 // that goes on has Z^(k) in zb(k), and zb(k - 1) is reset to Z0 to accumulate
-// Z^(k+1) (skipped after the last iteration).
+// Z^(k+1) (skipped after the last iteration).  Four frames per thread: 16-byte
+// accesses (a warp moves 512 bytes per variable); the frame count is a
+// multiple of 32, so groups of 4 never straddle it.  Frame flags are advanced
+// by the threads of the first variable slice.
 template <bool ES>
 __global__ void __launch_bounds__(256) f32s_cols(const DevCode c, F32S s, int k, int reset) {
-  const int f = blockIdx.y * 32 + (threadIdx.x & 31);
+  const int f0 = (blockIdx.y * 32 + (threadIdx.x & 31)) * 4;
+  if (f0 >= s.FL) return;
   const int cur = k & 1, nxt = cur ^ 1;
-  const uint32_t act = s.act[cur * s.FL + f];
-  const uint32_t stop = ES ? (act & (s.fail[cur * s.FL + f] ^ 1u)) : 0u;
-  const uint32_t cont = act & ~stop;
-  if (reset && cont) {
+  const uint4 act = *reinterpret_cast<const uint4*>(s.act + cur * s.FL + f0);
+  uint4 fail = make_uint4(0u, 0u, 0u, 0u);
+  if (ES) fail = *reinterpret_cast<const uint4*>(s.fail + cur * s.FL + f0);
+  const uint4 stop = ES ? make_uint4(act.x & (fail.x ^ 1u), act.y & (fail.y ^ 1u), act.z & (fail.z ^ 1u),
+                                     act.w & (fail.w ^ 1u))
+                        : make_uint4(0u, 0u, 0u, 0u);
+  const uint4 cont = make_uint4(act.x & ~stop.x, act.y & ~stop.y, act.z & ~stop.z, act.w & ~stop.w);
+  const bool all = (cont.x & cont.y & cont.z & cont.w) != 0u;
+  const bool any = (cont.x | cont.y | cont.z | cont.w) != 0u;
+  if (reset && any) {
     float* Zo = s.zb(k - 1);
+#pragma unroll 4
     for (int n = blockIdx.x * 8 + (threadIdx.x >> 5); n < c.N; n += gridDim.x * 8) {
-      const size_t o = (size_t)n * s.FL + f;
-      Zo[o] = s.q0[o];
+      const size_t o = (size_t)n * s.FL + f0;
+      const float4 q = *reinterpret_cast<const float4*>(s.q0 + o);
+      if (all) {
+        *reinterpret_cast<float4*>(Zo + o) = q;
+      } else {
+        if (cont.x) Zo[o] = q.x;
+        if (cont.y) Zo[o + 1] = q.y;
+        if (cont.z) Zo[o + 2] = q.z;
+        if (cont.w) Zo[o + 3] = q.w;
+      }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    s.act[nxt * s.FL + f] = cont;
-    s.fail[nxt * s.FL + f] = 0u;
-    if (ES && stop) {
-      s.iters[f] = k - 1;
-      s.ok[f] = 1u;
+  if (blockIdx.x == 0) {
+    *reinterpret_cast<uint4*>(s.act + nxt * s.FL + f0) = cont;
+    *reinterpret_cast<uint4*>(s.fail + nxt * s.FL + f0) = make_uint4(0u, 0u, 0u, 0u);
+    if (ES) {
+      const uint32_t st[4] = {stop.x, stop.y, stop.z, stop.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (st[q]) {
+          s.iters[f0 + q] = k - 1;
+          s.ok[f0 + q] = 1u;
+        }
+      }
     }
   }
 }
@@ -403,8 +428,8 @@ cudaError_t f32s_run(const DevCode& c, const F32Rule& r, const StreamLayout& L, 
   // group sizes differ)
   const RowGrid g2 = rows_grid_g(c.M, L.lanes, FORM == 1 ? kChunksSV : kChunksF32PE);
   const dim3 rgrid((unsigned)g2.x, (unsigned)g2.y);
-  const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / std::max(1, L.lanes / 32))),
-                   L.lanes / 32);
+  const int gy4 = (L.lanes / 4 + 31) / 32;  // groups of 32 threads x 4 frames
+  const dim3 cgrid((unsigned)std::max(1, std::min((c.N + 7) / 8, 4 * sm_count * 32 / gy4)), (unsigned)gy4);
   const bool wide = c.ell16 == nullptr;
   const bool c8 = c.ell_w <= 8;  // every check of degree <= 8: the 10-byte Section V state
   for (int k = 1; k <= max_iter; ++k) {

@@ -1,5 +1,5 @@
 """Pins of the oracle's sum-product check rule (the log-domain rule that
-min-sum approximates; SURVEY's accuracy reference), against what does not
+min-sum approximates; the accuracy reference of the min-sum decoders), against what does not
 depend on it:
 * cycle-free codes: the posteriors equal the exact a-posteriori LLRs (brute
   force over all codewords) after enough iterations;
