@@ -637,10 +637,11 @@ def main():
         wp["dtype"] = "f32"
     params = ldpc.make_params(form=args.form, kernel=args.kernel, schedule=args.schedule, **wp)
     ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
-    kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel"}.get(args.kernel)
+    kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel",
+             "cluster": "multi_h2_kernel"}.get(args.kernel)
     if args.schedule == "layered":
         kname = "layered_kernel"
-    elif ws_bytes > 0:
+    elif kname is None and ws_bytes > 0:
         kname = "f32s_rows" if args.dtype == "f32" else "h2s_rows"
     elif args.form == "two_scan":
         kname = "onchip_twoscan_kernel"
