@@ -131,9 +131,35 @@ KERNEL_SOURCES = {"onchip_h2_kernel": "onchip_h2.cu", "onchip_int8_kernel": "onc
                   "layered_kernel": "layered_h2.cu"}
 
 
+def code_text(src: str) -> str:
+    """C/C++/CUDA source without its comments and with whitespace runs collapsed:
+    what the compiler sees, so that editing a comment keeps the hash."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"' or c == "'":  # literal: copy through its closing quote
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash(kernel: str) -> str:
-    """Hash of the translation unit that defines ``kernel`` and of every local
-    header it includes (transitively): the sources its machine code comes from."""
+    """Hash of the code (comments left out) of the translation unit that defines
+    ``kernel`` and of every local header it includes (transitively): the sources
+    its machine code comes from."""
     csrc = os.path.join(ROOT, "paper_cs_0609090_gb300", "csrc")
     seen, todo = [], [os.path.join(csrc, KERNEL_SOURCES[kernel])]
     while todo:
@@ -146,7 +172,7 @@ def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     for f in sorted(seen, key=lambda x: os.path.relpath(x, ROOT)):
         h.update(os.path.relpath(f, ROOT).encode())
-        h.update(open(f, "rb").read())
+        h.update(code_text(open(f, encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

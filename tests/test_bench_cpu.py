@@ -30,24 +30,35 @@ def test_algorithmic_bytes_streaming_model():
 
 
 def test_source_hash_follows_the_translation_unit(tmp_path, monkeypatch):
-    """The hash covers the kernel's .cu file and every header it includes
-    (transitively), and nothing else."""
+    """The hash covers the code of the kernel's .cu file and of every header it
+    includes (transitively), and nothing else."""
     csrc = tmp_path / "paper_cs_0609090_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "a.cuh").write_text("// a\n")
+    (csrc / "a.cuh").write_text("int a;\n")
     (csrc / "b.h").write_text('#include "a.cuh"\n')
     (csrc / "k.cu").write_text('#include "b.h"\n// kernel\n')
-    (csrc / "other.cu").write_text("// unrelated\n")
+    (csrc / "other.cu").write_text("int unrelated;\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setitem(bench.KERNEL_SOURCES, "k_kernel", "k.cu")
     h0 = bench.kernel_source_hash("k_kernel")
-    (csrc / "other.cu").write_text("// changed\n")
+    (csrc / "other.cu").write_text("int changed;\n")
     assert bench.kernel_source_hash("k_kernel") == h0
-    (csrc / "a.cuh").write_text("// a changed\n")
+    (csrc / "a.cuh").write_text("int a2;\n")
     h1 = bench.kernel_source_hash("k_kernel")
     assert h1 != h0
-    (csrc / "k.cu").write_text('#include "b.h"\n// kernel changed\n')
-    assert bench.kernel_source_hash("k_kernel") not in (h0, h1)
+    (csrc / "k.cu").write_text('#include "b.h"\nint x = 1;\n')
+    h2 = bench.kernel_source_hash("k_kernel")
+    assert h2 not in (h0, h1)
+    # comments and layout are not code: editing them keeps the hash
+    (csrc / "k.cu").write_text('#include "b.h"  // the header\n/* a\n block */ int   x =\n 1;\n')
+    assert bench.kernel_source_hash("k_kernel") == h2
+    (csrc / "k.cu").write_text('#include "b.h"\nint x = 2;\n')
+    assert bench.kernel_source_hash("k_kernel") != h2
+
+
+def test_code_text_keeps_literals():
+    src = 'char* s = "a // b /* c */"; char q = \'\\\'\'; // gone\nint y; /* gone */ int z;'
+    assert bench.code_text(src) == 'char* s = "a // b /* c */"; char q = \'\\\'\'; int y; int z;'
 
 
 def test_committed_figures_are_well_formed():
