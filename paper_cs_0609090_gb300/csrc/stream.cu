@@ -5,21 +5,23 @@
 // warp -- consecutive frames -- read and atomically update consecutive words):
 //   int8 path, lane = frame pair, exact binary16 arithmetic (see h2ops.cuh):
 //     Zs [N][FP] half2, Acc [N][FP] i32 (lo + 65536 hi, biased like onchip_h2),
-//     state [M][FP] uint4 (Section V) or [ell_w M][FP] u16 (per-edge bytes
-//     L + 128 per edge slot j M + m of the degree-sorted table; by CSR edge in
-//     the fallback kernel),
+//     state [M][FP] (Section V: uint4, or uint2 when every check has degree
+//     <= 8) or [ell_w M][FP] u16 (per-edge bytes L + 128 per edge slot j M + m
+//     of the degree-sorted table; by CSR edge in the fallback kernel),
 //     q0 [N][FP] u16 (int8 pair), act/fail [2][FP] u32 bit masks, iters [2 FP]
 //   float path (stream_f32.cu), lane = frame:
-//     Z [2][N][FL] f32 (two posterior buffers), state [M][FL] uint4
-//     {A, B, n~, signs} or per-edge f32, q0 [N][FL] f32, act/fail [2][FL] u32,
-//     iters [FL]
-// Per iteration: a row kernel (one warp = one check for 32 lanes of frames; the
-// check's column indices are warp-uniform loads) then a column kernel that
-// applies the stop rule.  int8: the row kernel adds L^(k) - L^(k-1) to an
-// accumulator that always holds the current posterior (exact integer sums), so
-// the column kernel only converts it for the frames that continue; the CSR
-// fallback adds L^(k) and the column kernel resets the accumulator to Z0.  The
-// syndrome of x^(k-1) is computed by the row kernel of iteration k.
+//     Z [2][N][FL] f32 (two posterior buffers), state [M][FL] (Section V:
+//     uint4, or 10 bytes when every check has degree <= 8) or per-edge f32,
+//     q0 [N][FL] f32, act/fail [2][FL] u32, iters [FL]
+// Per iteration: a row kernel (one warp = kRowsPerWarp checks of the
+// degree-sorted order for 32 lanes; the checks' column indices are
+// warp-uniform loads; warp order per stream_grid.h) then a column kernel that
+// applies the stop rule, four lanes per thread.  int8: the row kernel adds
+// L^(k) - L^(k-1) to an accumulator that always holds the current posterior
+// (exact integer sums), so the column kernel only converts it for the frames
+// that continue; the CSR fallback adds L^(k) and its column kernel resets the
+// accumulator to Z0.  The syndrome of x^(k-1) is computed by the row kernel of
+// iteration k.
 #include <algorithm>
 
 #include "h2_body.cuh"
@@ -453,9 +455,11 @@ __global__ void __launch_bounds__(256) h2s_output(const DevCode c, H2S s, int kf
 // Per iteration: the degree-sorted row kernel with delta accumulation and the
 // converting column kernel (delta == true), or the CSR row kernel with the
 // resetting column kernel when 32-bit element offsets do not reach.  Measured
-// on the N=64800 staircase code (1024 frames, 50 iterations): 17.4 / 20.9 ms
-// (Section V / per-edge) with delta accumulation against 20.2 / 22.3 ms for
-// the best resetting kernels; 4 CTAs per SM beat 3 (19.1 / 21.3 ms) and 2.
+// on the N=64800 staircase code (1024 frames, 50 iterations), when delta
+// accumulation came in: 17.4 / 20.9 ms (Section V / per-edge) against 20.2 /
+// 22.3 ms for the best resetting kernels; 4 CTAs per SM beat 3 (19.1 / 21.3 ms)
+// and 2.  With the 8-byte state, chunk-major rows and the four-pair column
+// pass since: 14.4 / 18.7 ms.
 template <int FORM, bool ES>
 cudaError_t h2s_run(const DevCode& c, const IntRule& r, const StreamLayout& L, H2S s, int sm_count,
                     int32_t max_iter, bool delta, cudaStream_t st) {

@@ -4,9 +4,11 @@
 //
 // Workspace (StreamLayout, frame index innermost): two posterior buffers
 // [N][FL] f32 each, the message state [M][FL] uint4 {A, B, n~, signs}
-// (Section V) or per-edge f32 [slot][FL] (slot j M + m of the degree-sorted
-// table for min-sum, the CSR edge for sum-product), q0 [N][FL] f32, act/fail
-// [2][FL] u32, iters [FL], ok [FL].  The posterior accumulation uses
+// (Section V; 10 bytes per frame when every check has degree <= 8) or per-edge
+// f32 [slot][FL] (slot j M + m of the degree-sorted table for min-sum, the CSR
+// edge for sum-product), q0 [N][FL] f32, act/fail [2][FL] u32, iters [FL],
+// ok [FL].  The row passes run chunk-major (stream_grid.h), the column pass
+// takes four frames per thread.  The posterior accumulation uses
 // floating-point atomics, so its rounding depends on the order of the additions.
 #include <algorithm>
 
