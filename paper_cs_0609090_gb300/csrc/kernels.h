@@ -112,8 +112,9 @@ struct StreamLayout {
   int lanes = 0;  // frame pairs (int8) or frames (float32), padded to 32
   size_t z = 0, acc = 0, st = 0, q0 = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
 };
-// E: message slots of the per-edge form (int8: ell_w * M edge slots of the
-// degree-sorted table; float32: the E edges of H).
+// E: message slots of the per-edge form (the degree-sorted table's ell_w * M;
+// float32 gets max(E, ell_w * M), its sum-product rule addressing the E edges
+// of H).
 StreamLayout stream_layout(int dtype, int form, int N, int M, int E, int F);
 bool stream_int8_eligible(int max_row_deg, int max_col_deg, int qm);
 cudaError_t stream_int8_decode(const DevCode& c, const IntRule& r, int form, const StreamLayout& L, void* ws,
