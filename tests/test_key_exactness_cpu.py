@@ -1,9 +1,11 @@
 """The min-search key of the packed check body, checked exhaustively on the CPU:
 one saturating binary16 multiply-add fma.rn.sat(|u|, 2^-7, j 2^-11) forms
 (16 |u| + j) 2^-11 clamped to 1, and the minima start at (16 Qm + 15) 2^-11.
-The claim the kernels rest on: the decoded minimum of any set of positions is
-16 min(|u|, Qm) + j of the first position reaching it, for every Qm in [1, 127]
-and every |u| a binary16 posterior difference can take (< 2048).
+The claim the kernels rest on: the decoded minimum of any set of positions has
+the magnitude min(|u|, Qm) of the smallest, and the first position reaching it
+wherever that magnitude is below Qm (where both minima saturate, A = B and the
+position does not matter), for every Qm in [1, 127] and every |u| a binary16
+posterior difference can take (< 2048).
 
 fma.rn rounds the exact a b + c once; here the exact value (16 |u| + j) / 2048
 is formed in float64 (exact) and rounded once to binary16 by numpy, which
