@@ -373,15 +373,22 @@ LDPC_API ldpc_status ldpc_multi_workspace_size(const ldpc_multi *plan, size_t *b
  * counters, the persistent kernel launch, and the streaming decoder's memsets
  * and launches for the codes that run on it; no allocation, no host
  * synchronisation, so the call can be captured in a CUDA graph and replayed.
- * workspace: device, 256-byte aligned, at least ldpc_multi_workspace_size
- * bytes, not shared with another call in flight. */
+ * When the plan overlaps its streamed codes (chosen by ldpc_multi_autotune),
+ * they run on side streams of the plan, forked from `stream` with an event
+ * after the persistent kernel and joined back into it with one event each,
+ * so the call still orders as one unit on `stream` (and captures as a fork /
+ * join in a graph); the plan's first such call creates those streams and
+ * events.  workspace: device, 256-byte aligned, at least
+ * ldpc_multi_workspace_size bytes, not shared with another call in flight. */
 LDPC_API ldpc_status ldpc_multi_decode(const ldpc_multi *plan, void *workspace, size_t ws_bytes, void *stream);
 
 /* Times the candidate launch shapes (threads, team_threads, large, cluster) on the
  * plan's own buffers, reps decodes each after one warm-up, with CUDA events on
- * `stream` (synchronising it), and keeps the fastest.  The decodes overwrite
- * the outputs (with the same values).  Not capturable.  chosen (host,
- * nullable) receives the kept shape, best_ms (host, nullable) its mean time. */
+ * `stream` (synchronising it), and keeps the fastest; then times that shape
+ * with the streamed codes in sequence and overlapped (at least 5 decodes
+ * each, back to back) and keeps the faster.  The decodes overwrite the
+ * outputs (with the same values).  Not capturable.  chosen (host, nullable)
+ * receives the kept shape, best_ms (host, nullable) its mean time. */
 LDPC_API ldpc_status ldpc_multi_autotune(ldpc_multi *plan, void *workspace, size_t ws_bytes, int32_t reps,
                                          void *stream, ldpc_multi_tuning *chosen, float *best_ms);
 

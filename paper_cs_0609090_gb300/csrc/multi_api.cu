@@ -341,14 +341,18 @@ cudaError_t ensure_side(const ldpc_multi* p) {
     cudaError_t e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
   }
+  // a stream and its join event are added together, so the two lists stay in step
   while (p->side.size() < p->streamed.size()) {
     cudaStream_t s;
     cudaEvent_t ev;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
-    p->side.push_back(s);
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(s);
+      return e;
+    }
+    p->side.push_back(s);
     p->joined.push_back(ev);
   }
   return cudaSuccess;
@@ -525,6 +529,8 @@ ldpc_status ldpc_multi_create(ldpc_multi** out, const ldpc_multi_job* jobs, int3
 
 ldpc_status ldpc_multi_destroy(ldpc_multi* plan) {
   clear_error();
+  if (plan == nullptr) return LDPC_OK;
+  DeviceGuard guard(plan->device);  // its side streams and events belong to that device
   delete plan;
   return LDPC_OK;
 }
