@@ -126,7 +126,7 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-KERNEL_SOURCES = {"onchip_h2_kernel": "onchip_h2.cu", "onchip_int8_kernel": "onchip_int8.cu",
+KERNEL_SOURCES = {"onchip_h2_kernel": "onchip_h2.cu", "onchip_int8_kernel": "onchip_int8.cu", "pp_kernel": "persist.cu",
                   "onchip_twoscan_kernel": "onchip_twoscan.cu", "h2s_rows": "stream.cu", "f32s_rows": "stream_f32.cu",
                   "layered_kernel": "layered_h2.cu"}
 
@@ -622,7 +622,8 @@ def main():
     ap.add_argument("--workload", default="qc_n7493")
     ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "onchip_int", "onchip_half", "stream", "cluster"])
+    ap.add_argument("--kernel", default="auto",
+                    choices=["auto", "onchip_int", "onchip_half", "stream", "cluster", "persistent"])
     ap.add_argument("--dtype", default="int8", choices=["int8", "f32"])
     ap.add_argument("--schedule", default="flooding", choices=["flooding", "layered"],
                     help="layered: the single scan with column-disjoint layers updating in place")
@@ -663,8 +664,9 @@ def main():
         wp["dtype"] = "f32"
     params = ldpc.make_params(form=args.form, kernel=args.kernel, schedule=args.schedule, **wp)
     ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
+    chosen = ldpc.ldpc_kernel_choice(code.handle, params, F)
     kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel",
-             "cluster": "multi_h2_kernel"}.get(args.kernel)
+             "cluster": "multi_h2_kernel", "persistent": "pp_kernel"}.get(chosen if args.kernel == "auto" else args.kernel)
     if args.schedule == "layered":
         kname = "layered_kernel"
     elif kname is None and ws_bytes > 0:
@@ -815,13 +817,13 @@ def main():
                        "ebn0_db": w.ebn0_db, "rule": w.params["rule"], "early_stop": w.params["early_stop"],
                        "mean_iters": mean_iters,
                        "l2": "flushed between timed steps (256 MB write)", "frames_per_rank": F,
-                       "kernel": args.kernel, "schedule": args.schedule},
+                       "kernel": args.kernel, "kernel_chosen": chosen, "schedule": args.schedule},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(host_llr.nbytes),
                     "d2h_bytes_per_step": int(bits.numel() + iters.numel() * 4 + ok.numel()),
                     "mode": e2e_mode, "pipelined_value": e2e_pipe, "serial_value": e2e_serial,
                     "pipeline": "upload and read-back streams: step s+1's input copy overlaps step s's decode"},
             "gpu_launches": args.steps * (1 if (ws_bytes == 0 or args.schedule == "layered")
-                                          else 3 + 2 * w.params["max_iter"]),
+                                          else 2 if kname == "pp_kernel" else 3 + 2 * w.params["max_iter"]),
             "roofline": roofline, "clocks": clocks}
     if not args.no_cpu_baseline and args.dtype == "int8":
         lay = ldpc.ldpc_code_layers(code.handle, w.code.n_checks)[1] if args.schedule == "layered" else None

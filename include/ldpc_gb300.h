@@ -90,8 +90,20 @@ enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2, LDPC
  *                                         128 + (max_col_degree + 1) * msg_sat <= 2048
  *                                         and n_vars <= 65535)
  *                LDPC_KERNEL_STREAM       frame state in device memory (the
- *                                         workspace); for codes too large for one
+ *                                         workspace), two kernel launches per
+ *                                         iteration; for codes too large for one
  *                                         SM; the only kernel of the float32 path
+ *                LDPC_KERNEL_PERSISTENT   frame state in the workspace, the whole
+ *                                         decode in one persistent kernel launch
+ *                                         that takes groups of 64-frame chunks
+ *                                         through all their iterations while
+ *                                         their state stays in L2; int8, the
+ *                                         binary16 conditions of ONCHIP_HALF and
+ *                                         row degree <= 16.  Its waits between work items
+ *                                         are bounded: if one gives up (it does
+ *                                         not in a correct run), every frame of
+ *                                         the call reports iters_used = -1 and
+ *                                         syndrome_ok = 0
  *                LDPC_KERNEL_CLUSTER      a frame pair spread over the CTAs of a
  *                                         thread-block cluster (distributed shared
  *                                         memory), the packed binary16 arithmetic
@@ -133,7 +145,8 @@ enum {
   LDPC_KERNEL_ONCHIP_INT = 1,
   LDPC_KERNEL_ONCHIP_HALF = 2,
   LDPC_KERNEL_STREAM = 3,
-  LDPC_KERNEL_CLUSTER = 4
+  LDPC_KERNEL_CLUSTER = 4,
+  LDPC_KERNEL_PERSISTENT = 5
 };
 
 /* Build a code from the check->variable adjacency N(m) of H (Section II).
@@ -160,6 +173,13 @@ LDPC_API ldpc_status ldpc_code_info(const ldpc_code *code, int32_t *n_vars, int3
  * 0 when the chosen kernel keeps all per-frame state on chip. */
 LDPC_API ldpc_status ldpc_workspace_size(const ldpc_code *code, const ldpc_decode_params *params,
                                 int32_t n_frames, size_t *bytes);
+
+/* The implementation (an LDPC_KERNEL_* value other than AUTO) that
+ * ldpc_decode_batch runs for this request: params->kernel itself when it is
+ * not AUTO, else the library's choice.  For the layered schedule *kernel is
+ * LDPC_KERNEL_AUTO (it has one implementation).  Errors as ldpc_workspace_size. */
+LDPC_API ldpc_status ldpc_kernel_choice(const ldpc_code *code, const ldpc_decode_params *params,
+                                        int32_t n_frames, int32_t *kernel);
 
 /* Decode a batch of frames (Sections III-V).
  *   llr          device, frame-major [n_frames][n_vars] channel values Z0_n,
@@ -399,6 +419,14 @@ LDPC_API ldpc_status ldpc_multi_autotune(ldpc_multi *plan, void *workspace, size
 LDPC_API ldpc_status ldpc_multi_info(const ldpc_multi *plan, ldpc_multi_tuning *shape, int32_t *grid,
                                      int32_t *cluster, int32_t *smem_bytes, int32_t *job_is_cluster,
                                      int32_t *job_pairs_per_cta);
+
+/* Diagnostic of the persistent decoder's failure path: on `device`, one CTA runs
+ * the bounded wait that the decoder uses between its work items, on a counter
+ * that nothing increments, for max_spins polls (128 ns apart; 1 .. 2^24).  The
+ * wait gives up, sets the error word and returns, so the expected result is
+ * LDPC_ERR_TIMEOUT; the CUDA context stays usable.  Synchronous; allocates a
+ * few hundred bytes of device memory for the call. */
+LDPC_API ldpc_status ldpc_wait_selftest(int device, int32_t max_spins);
 
 /* Message describing the last failed call on this thread ("" if none). */
 LDPC_API const char *ldpc_last_error(void);

@@ -124,6 +124,26 @@ cudaError_t stream_f32_decode(const DevCode& c, const F32Rule& r, int form, cons
                               int sm_count, const float* llr, int32_t F, int32_t max_iter, int32_t early_stop,
                               uint8_t* bits, int32_t* iters, uint8_t* ok, float* zout, cudaStream_t st);
 
+// The persistent streaming decoder (persist.cu): one kernel launch per decode,
+// a work queue over (chunk of 32 frame pairs, iteration, tile of checks) that
+// runs groups of W chunks through all their iterations while their state stays
+// in L2; two posterior buffers updated with exact f16x2 atomics, no column pass.
+struct PersistLayout {
+  int lanes = 0, chunks = 0, W = 1;
+  bool c8 = false;     // Section V state in 8 bytes per pair (every check degree <= 8)
+  int ub = 0;          // bytes per state unit and pair (8 / 16, or 2 for a per-edge message)
+  int rows = 0;        // state units per buffer: M (Section V) or ell_w M (per edge)
+  size_t zb = 0, st = 0, act = 0, fail = 0, iters = 0, ok = 0, ctl = 0, total = 0;
+};
+PersistLayout persist_layout(int form, int N, int M, int ell_w, int F, int group_chunks);
+bool persist_int8_eligible(int N, int M, int ell_w, int max_row_deg, int max_col_deg, int qm, int form, int F);
+cudaError_t persist_int8_decode(const DevCode& c, const IntRule& r, int form, const PersistLayout& L, void* ws,
+                                int sm_count, const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop,
+                                uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st);
+// Runs the queue's bounded wait on a counter that nothing increments (one CTA,
+// max_spins polls) and reports whether it gave up.  Synchronous.
+cudaError_t persist_wait_selftest(uint32_t max_spins, bool* gave_up);
+
 // Learned offsets beta[k][class]: workspace layout and launchers (learned.cu).
 struct LearnedLayout {
   int FL = 0, tasks = 0;

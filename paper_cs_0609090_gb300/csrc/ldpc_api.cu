@@ -125,7 +125,7 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   if (p->max_iter < 0) return fail(LDPC_ERR_INVALID_ARG, "max_iter %d < 0", p->max_iter);
   if (p->early_stop != 0 && p->early_stop != 1)
     return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");
-  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_CLUSTER)
+  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_PERSISTENT)
     return fail(LDPC_ERR_INVALID_ARG, "kernel %d is not a known LDPC_KERNEL_*", p->kernel);
   if (p->schedule != LDPC_SCHEDULE_FLOODING && p->schedule != LDPC_SCHEDULE_LAYERED)
     return fail(LDPC_ERR_INVALID_ARG, "schedule %d is not a known LDPC_SCHEDULE_*", p->schedule);
@@ -158,11 +158,20 @@ using namespace ldpc_api;
 
 namespace {
 
+// Chunks of 32 frame pairs that the persistent decoder takes through all their
+// iterations together (their state stays in L2 meanwhile).
+#ifndef LDPC_PP_GROUP_CHUNKS
+#define LDPC_PP_GROUP_CHUNKS 2
+#endif
+constexpr int kPersistGroupChunks = LDPC_PP_GROUP_CHUNKS;
+
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
-  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, STREAM_F32, ONCHIP_TWOSCAN, LAYERED } kind = NONE;
+  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, PERSIST_INT8, STREAM_F32, ONCHIP_TWOSCAN,
+              LAYERED } kind = NONE;
   ldpc::OnchipPlan onchip;
   ldpc::StreamLayout stream;
+  ldpc::PersistLayout persist;
   ldpc::LayeredLayout layered;
   size_t ws = 0;
 };
@@ -188,6 +197,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     const bool want_int = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_INT;
     const bool want_stream = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM;
     const bool want_cluster = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_CLUSTER;
+    const bool want_persist = p->kernel == LDPC_KERNEL_PERSISTENT;
     if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num) &&
         ldpc::onchip_h2_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_H2;
@@ -202,6 +212,13 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     if (want_int && ldpc::onchip_int8_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_INT8;
       ch->ws = 0;
+      return LDPC_OK;
+    }
+    if (want_persist && ldpc::persist_int8_eligible(c->N, c->M, c->ell_w, c->max_row_deg, c->max_col_deg,
+                                                    p->msg_sat, form, n_frames)) {
+      ch->kind = Choice::PERSIST_INT8;
+      ch->persist = ldpc::persist_layout(form, c->N, c->M, c->ell_w, n_frames, kPersistGroupChunks);
+      ch->ws = ch->persist.total;
       return LDPC_OK;
     }
     if (want_stream && ldpc::stream_int8_eligible(c->max_row_deg, c->max_col_deg, p->msg_sat)) {
@@ -465,6 +482,30 @@ ldpc_status ldpc_workspace_size(const ldpc_code* code, const ldpc_decode_params*
   return LDPC_OK;
 }
 
+ldpc_status ldpc_kernel_choice(const ldpc_code* code, const ldpc_decode_params* params, int32_t n_frames,
+                               int32_t* kernel) {
+  g_last_error.clear();
+  if (code == nullptr || params == nullptr || kernel == nullptr)
+    return fail(LDPC_ERR_INVALID_ARG, "code, params and kernel must be non-NULL");
+  if (n_frames < 0) return fail(LDPC_ERR_INVALID_ARG, "n_frames %d < 0", n_frames);
+  ldpc_status s = check_params(code, params);
+  if (s != LDPC_OK) return s;
+  Choice ch;
+  s = choose(code, params, n_frames > 0 ? n_frames : 1, &ch);
+  if (s != LDPC_OK) return s;
+  switch (ch.kind) {
+    case Choice::ONCHIP_INT8: *kernel = LDPC_KERNEL_ONCHIP_INT; break;
+    case Choice::ONCHIP_H2:
+    case Choice::ONCHIP_TWOSCAN: *kernel = LDPC_KERNEL_ONCHIP_HALF; break;
+    case Choice::CLUSTER_H2: *kernel = LDPC_KERNEL_CLUSTER; break;
+    case Choice::STREAM_INT8:
+    case Choice::STREAM_F32: *kernel = LDPC_KERNEL_STREAM; break;
+    case Choice::PERSIST_INT8: *kernel = LDPC_KERNEL_PERSISTENT; break;
+    default: *kernel = LDPC_KERNEL_AUTO; break;
+  }
+  return LDPC_OK;
+}
+
 ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* params, const void* llr,
                               int32_t n_frames, uint8_t* hard_bits, int32_t* iters_used, uint8_t* syndrome_ok,
                               void* llr_out, void* workspace, size_t ws_bytes, void* stream) {
@@ -516,6 +557,10 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
     err = ldpc::stream_int8_decode(v, r, form, ch.stream, workspace, code->sm_count, static_cast<const int8_t*>(llr),
                                    n_frames, params->max_iter, params->early_stop, hard_bits, iters_used,
                                    syndrome_ok, static_cast<int16_t*>(llr_out), st);
+  } else if (ch.kind == Choice::PERSIST_INT8) {
+    err = ldpc::persist_int8_decode(v, r, form, ch.persist, workspace, code->sm_count,
+                                    static_cast<const int8_t*>(llr), n_frames, params->max_iter, params->early_stop,
+                                    hard_bits, iters_used, syndrome_ok, static_cast<int16_t*>(llr_out), st);
   } else if (ch.kind == Choice::STREAM_F32) {
     ldpc::F32Rule fr;
     fr.rule = params->rule;
@@ -656,6 +701,18 @@ ldpc_status ldpc_quantize_llr(const float* llr, int64_t n, float delta, int32_t 
   if (n == 0) return LDPC_OK;
   const cudaError_t e = ldpc::quantize_llr(llr, (size_t)n, delta, qc, q, (cudaStream_t)stream);
   return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_quantize_llr launch");
+}
+
+ldpc_status ldpc_wait_selftest(int device, int32_t max_spins) {
+  g_last_error.clear();
+  if (max_spins < 1 || max_spins > (1 << 24)) return fail(LDPC_ERR_INVALID_ARG, "max_spins %d outside [1, 2^24]", max_spins);
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(LDPC_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+  bool gave_up = false;
+  const cudaError_t e = ldpc::persist_wait_selftest((uint32_t)max_spins, &gave_up);
+  if (e != cudaSuccess) return cuda_fail(e, "ldpc_wait_selftest");
+  if (gave_up) return fail(LDPC_ERR_TIMEOUT, "the bounded wait gave up after %d polls", max_spins);
+  return LDPC_OK;
 }
 
 // ---------------------------------------------------------------------------

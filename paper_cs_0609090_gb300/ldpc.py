@@ -28,11 +28,12 @@ DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_
 FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
 RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED,
          "sum_product": LDPC_RULE_SUM_PRODUCT}
-LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM, LDPC_KERNEL_CLUSTER = range(5)
+(LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM, LDPC_KERNEL_CLUSTER,
+ LDPC_KERNEL_PERSISTENT) = range(6)
 LDPC_SCHEDULE_FLOODING, LDPC_SCHEDULE_LAYERED = 0, 1
 SCHEDULES = {"flooding": LDPC_SCHEDULE_FLOODING, "layered": LDPC_SCHEDULE_LAYERED}
 KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF,
-           "stream": LDPC_KERNEL_STREAM, "cluster": LDPC_KERNEL_CLUSTER}
+           "stream": LDPC_KERNEL_STREAM, "cluster": LDPC_KERNEL_CLUSTER, "persistent": LDPC_KERNEL_PERSISTENT}
 
 # Every symbol include/ldpc_gb300.h declares.
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",
@@ -40,7 +41,8 @@ EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_work
            "ldpc_learned_workspace_size", "ldpc_learned_forward", "ldpc_learned_loss", "ldpc_learned_backward",
            "ldpc_adam_step", "ldpc_awgn_llr_f32", "ldpc_quantize_llr", "ldpc_multi_create", "ldpc_multi_destroy",
            "ldpc_multi_workspace_size", "ldpc_multi_decode", "ldpc_multi_autotune", "ldpc_multi_info",
-           "ldpc_code_layers", "ldpc_code_set_layers", "ldpc_last_error")
+           "ldpc_code_layers", "ldpc_code_set_layers", "ldpc_wait_selftest", "ldpc_kernel_choice",
+           "ldpc_last_error")
 NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -100,6 +102,8 @@ _lib.ldpc_multi_decode.argtypes = [_P, _P, ctypes.c_size_t, _P]
 _lib.ldpc_multi_autotune.argtypes = [_P, _P, ctypes.c_size_t, ctypes.c_int32, _P, ctypes.POINTER(ldpc_multi_tuning),
                                      ctypes.POINTER(ctypes.c_float)]
 _lib.ldpc_multi_info.argtypes = [_P, ctypes.POINTER(ldpc_multi_tuning), _P, _P, _P, _P, _P]
+_lib.ldpc_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_int32]
+_lib.ldpc_kernel_choice.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), ctypes.c_int32, _P]
 _lib.ldpc_last_error.restype = ctypes.c_char_p
 for _f in EXPORTS[:-1]:
     getattr(_lib, _f).restype = ctypes.c_int32
@@ -125,6 +129,20 @@ def _stream_handle(stream):
     if hasattr(stream, "cuda_stream"):
         return _P(stream.cuda_stream)
     return _P(int(stream))
+
+
+def ldpc_kernel_choice(code: int, params: ldpc_decode_params, n_frames: int) -> str:
+    """Name (a KERNELS key) of the implementation ldpc_decode_batch runs."""
+    out = ctypes.c_int32(0)
+    _check(_lib.ldpc_kernel_choice(_P(code), ctypes.byref(params), int(n_frames), ctypes.byref(out)),
+           "ldpc_kernel_choice")
+    return {v: k for k, v in KERNELS.items()}[out.value]
+
+
+def ldpc_wait_selftest(device: int, max_spins: int) -> int:
+    """Status of the persistent decoder's bounded wait run on a counter that
+    nothing increments (LDPC_ERR_TIMEOUT is the expected answer)."""
+    return int(_lib.ldpc_wait_selftest(int(device), int(max_spins)))
 
 
 def ldpc_last_error() -> str:

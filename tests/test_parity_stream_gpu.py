@@ -37,36 +37,46 @@ def _int(L, code, q0, form, p, kernel="stream"):
     return g
 
 
+STREAM_KERNELS = ("stream", "persistent")
+
+
+@pytest.mark.parametrize("kernel", STREAM_KERNELS)
 @pytest.mark.parametrize("form", FORMS_INT)
 @pytest.mark.parametrize("early_stop", [1, 0])
-def test_int8_stream_small_codes(L, form, early_stop):
+def test_int8_stream_small_codes(L, form, early_stop, kernel):
+    """301 frames of the N=1008 code: 151 frame pairs, 5 chunks of 32 pairs, so
+    the persistent decoder runs two full groups of two chunks and a last group of
+    one, with a ragged last chunk and an odd frame count."""
     w = I.make_workload("reg36_n1008", n_frames=301, ebn0_db=1.8)
-    _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop))
+    _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop), kernel=kernel)
     w = I.make_workload("qc_n7493", n_frames=67, ebn0_db=2.0)
-    _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop))
+    _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop), kernel=kernel)
 
 
+@pytest.mark.parametrize("kernel", STREAM_KERNELS)
 @pytest.mark.parametrize("form", FORMS_INT)
-def test_int8_stream_edge_cases(L, form):
+def test_int8_stream_edge_cases(L, form, kernel):
     w = I.make_workload("reg36_n1008", n_frames=65, ebn0_db=1.0)
     for F in (1, 2, 33, 65):
-        _int(L, w.code, w.q0[:F], form, w.params)
-    _int(L, w.code, w.q0[:5], form, dict(w.params, max_iter=0))
-    g = _int(L, w.code, I.noiseless(w.codewords, 31), form, w.params)
+        _int(L, w.code, w.q0[:F], form, w.params, kernel=kernel)
+    _int(L, w.code, w.q0[:5], form, dict(w.params, max_iter=0), kernel=kernel)
+    _int(L, w.code, w.q0[:5], form, dict(w.params, max_iter=1), kernel=kernel)
+    _int(L, w.code, w.q0[:5], form, dict(w.params, max_iter=0, early_stop=0), kernel=kernel)
+    g = _int(L, w.code, I.noiseless(w.codewords, 31), form, w.params, kernel=kernel)
     assert np.all(g["iters"] == 0)
 
 
 @pytest.mark.parametrize("form", FORMS_INT)
 @pytest.mark.parametrize("early_stop", [1, 0])
 def test_int8_irregular_64800(L, form, early_stop):
-    """The N=64800 code does not fit one SM: the streaming kernel (the library's
-    choice) and the cluster kernel (8 CTAs, distributed shared memory) both
-    decode it."""
+    """The N=64800 code does not fit one SM: the two-launch streaming kernel (the
+    library's choice), the persistent streaming kernel and the cluster kernel
+    (8 CTAs, distributed shared memory) all decode it."""
     w = I.make_workload("irr_n64800", n_frames=7, frame_seed=3)
     p = dict(w.params, early_stop=early_stop)
     h = L.Code.from_inputs(w.code)
     assert L.ldpc_workspace_size(h.handle, L.make_params(form=form, **p), 7) > 0
-    for kern in ("auto", "cluster"):
+    for kern in ("auto", "persistent", "stream", "cluster"):
         _int(L, w.code, w.q0, form, p, kernel=kern)
         if early_stop:
             q = I.noiseless(w.codewords[:2], 127)
