@@ -126,7 +126,7 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-KERNEL_SOURCES = {"onchip_h2_kernel": "onchip_h2.cu", "onchip_int8_kernel": "onchip_int8.cu", "pp_kernel": "persist.cu",
+KERNEL_SOURCES = {"onchip_h2_kernel": "onchip_h2.cu", "onchip_int8_kernel": "onchip_int8.cu", "pp_kernel": "persist.cu", "pp2_rows": "pingpong.cu",
                   "onchip_twoscan_kernel": "onchip_twoscan.cu", "h2s_rows": "stream.cu", "f32s_rows": "stream_f32.cu",
                   "layered_kernel": "layered_h2.cu"}
 
@@ -623,7 +623,7 @@ def main():
     ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto",
-                    choices=["auto", "onchip_int", "onchip_half", "stream", "cluster", "persistent"])
+                    choices=["auto", "onchip_int", "onchip_half", "stream", "cluster", "persistent", "pingpong"])
     ap.add_argument("--dtype", default="int8", choices=["int8", "f32"])
     ap.add_argument("--schedule", default="flooding", choices=["flooding", "layered"],
                     help="layered: the single scan with column-disjoint layers updating in place")
@@ -666,7 +666,8 @@ def main():
     ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
     chosen = ldpc.ldpc_kernel_choice(code.handle, params, F)
     kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel",
-             "cluster": "multi_h2_kernel", "persistent": "pp_kernel"}.get(chosen if args.kernel == "auto" else args.kernel)
+             "cluster": "multi_h2_kernel", "persistent": "pp_kernel", "pingpong": "pp2_rows"}.get(
+                 chosen if args.kernel == "auto" else args.kernel)
     if args.schedule == "layered":
         kname = "layered_kernel"
     elif kname is None and ws_bytes > 0:
@@ -823,7 +824,9 @@ def main():
                     "mode": e2e_mode, "pipelined_value": e2e_pipe, "serial_value": e2e_serial,
                     "pipeline": "upload and read-back streams: step s+1's input copy overlaps step s's decode"},
             "gpu_launches": args.steps * (1 if (ws_bytes == 0 or args.schedule == "layered")
-                                          else 2 if kname == "pp_kernel" else 3 + 2 * w.params["max_iter"]),
+                                          else 2 if kname == "pp_kernel"
+                                          else 3 + w.params["max_iter"] if kname == "pp2_rows"
+                                          else 3 + 2 * w.params["max_iter"]),
             "roofline": roofline, "clocks": clocks}
     if not args.no_cpu_baseline and args.dtype == "int8":
         lay = ldpc.ldpc_code_layers(code.handle, w.code.n_checks)[1] if args.schedule == "layered" else None

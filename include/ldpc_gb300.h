@@ -93,6 +93,16 @@ enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2, LDPC
  *                                         workspace), two kernel launches per
  *                                         iteration; for codes too large for one
  *                                         SM; the only kernel of the float32 path
+ *                LDPC_KERNEL_PINGPONG     frame state in the workspace, one kernel
+ *                                         launch per iteration and no column
+ *                                         pass: two posterior buffers, the one
+ *                                         read (Z^(k-1)) and the one updated
+ *                                         with the exact binary16 sums of
+ *                                         L^(k) - L^(k-2); two frame pairs per
+ *                                         lane; int8, check degree <= 8 and the
+ *                                         binary16 condition of ONCHIP_HALF;
+ *                                         what AUTO runs for int8 single-scan
+ *                                         codes too large for one SM
  *                LDPC_KERNEL_PERSISTENT   frame state in the workspace, the whole
  *                                         decode in one persistent kernel launch
  *                                         that takes groups of 64-frame chunks
@@ -146,7 +156,8 @@ enum {
   LDPC_KERNEL_ONCHIP_HALF = 2,
   LDPC_KERNEL_STREAM = 3,
   LDPC_KERNEL_CLUSTER = 4,
-  LDPC_KERNEL_PERSISTENT = 5
+  LDPC_KERNEL_PERSISTENT = 5,
+  LDPC_KERNEL_PINGPONG = 6
 };
 
 /* Build a code from the check->variable adjacency N(m) of H (Section II).

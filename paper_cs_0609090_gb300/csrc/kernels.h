@@ -124,6 +124,21 @@ cudaError_t stream_f32_decode(const DevCode& c, const F32Rule& r, int form, cons
                               int sm_count, const float* llr, int32_t F, int32_t max_iter, int32_t early_stop,
                               uint8_t* bits, int32_t* iters, uint8_t* ok, float* zout, cudaStream_t st);
 
+// The ping-pong streaming decoder (pingpong.cu): one kernel launch per
+// iteration, two posterior buffers accumulated with exact f16x2 atomics (no
+// column pass), two frame pairs per lane; codes whose checks have degree <= 8.
+struct PingpongLayout {
+  int lanes = 0;   // frame pairs, padded to 64
+  int ub = 0;      // bytes per state unit and pair (8: Section V; 2: a per-edge message)
+  int rows = 0;    // state units per buffer: M (Section V) or ell_w M (per edge)
+  size_t zb = 0, st = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
+};
+PingpongLayout pingpong_layout(int form, int N, int M, int ell_w, int F);
+bool pingpong_int8_eligible(int N, int M, int ell_w, int max_row_deg, int max_col_deg, int qm, int form, int F);
+cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, const PingpongLayout& L, void* ws,
+                                 const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
+                                 int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st);
+
 // The persistent streaming decoder (persist.cu): one kernel launch per decode,
 // a work queue over (chunk of 32 frame pairs, iteration, tile of checks) that
 // runs groups of W chunks through all their iterations while their state stays

@@ -125,7 +125,7 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   if (p->max_iter < 0) return fail(LDPC_ERR_INVALID_ARG, "max_iter %d < 0", p->max_iter);
   if (p->early_stop != 0 && p->early_stop != 1)
     return fail(LDPC_ERR_INVALID_ARG, "early_stop must be 0 or 1");
-  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_PERSISTENT)
+  if (p->kernel < LDPC_KERNEL_AUTO || p->kernel > LDPC_KERNEL_PINGPONG)
     return fail(LDPC_ERR_INVALID_ARG, "kernel %d is not a known LDPC_KERNEL_*", p->kernel);
   if (p->schedule != LDPC_SCHEDULE_FLOODING && p->schedule != LDPC_SCHEDULE_LAYERED)
     return fail(LDPC_ERR_INVALID_ARG, "schedule %d is not a known LDPC_SCHEDULE_*", p->schedule);
@@ -167,11 +167,12 @@ constexpr int kPersistGroupChunks = LDPC_PP_GROUP_CHUNKS;
 
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
-  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, PERSIST_INT8, STREAM_F32, ONCHIP_TWOSCAN,
-              LAYERED } kind = NONE;
+  enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, PERSIST_INT8, PINGPONG_INT8, STREAM_F32,
+              ONCHIP_TWOSCAN, LAYERED } kind = NONE;
   ldpc::OnchipPlan onchip;
   ldpc::StreamLayout stream;
   ldpc::PersistLayout persist;
+  ldpc::PingpongLayout pingpong;
   ldpc::LayeredLayout layered;
   size_t ws = 0;
 };
@@ -198,6 +199,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     const bool want_stream = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM;
     const bool want_cluster = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_CLUSTER;
     const bool want_persist = p->kernel == LDPC_KERNEL_PERSISTENT;
+    const bool want_pingpong = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_PINGPONG;
     if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num) &&
         ldpc::onchip_h2_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_H2;
@@ -212,6 +214,13 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
     if (want_int && ldpc::onchip_int8_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_INT8;
       ch->ws = 0;
+      return LDPC_OK;
+    }
+    if (want_pingpong && ldpc::pingpong_int8_eligible(c->N, c->M, c->ell_w, c->max_row_deg, c->max_col_deg,
+                                                      p->msg_sat, form, n_frames)) {
+      ch->kind = Choice::PINGPONG_INT8;
+      ch->pingpong = ldpc::pingpong_layout(form, c->N, c->M, c->ell_w, n_frames);
+      ch->ws = ch->pingpong.total;
       return LDPC_OK;
     }
     if (want_persist && ldpc::persist_int8_eligible(c->N, c->M, c->ell_w, c->max_row_deg, c->max_col_deg,
@@ -501,6 +510,7 @@ ldpc_status ldpc_kernel_choice(const ldpc_code* code, const ldpc_decode_params* 
     case Choice::STREAM_INT8:
     case Choice::STREAM_F32: *kernel = LDPC_KERNEL_STREAM; break;
     case Choice::PERSIST_INT8: *kernel = LDPC_KERNEL_PERSISTENT; break;
+    case Choice::PINGPONG_INT8: *kernel = LDPC_KERNEL_PINGPONG; break;
     default: *kernel = LDPC_KERNEL_AUTO; break;
   }
   return LDPC_OK;
@@ -557,6 +567,10 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
     err = ldpc::stream_int8_decode(v, r, form, ch.stream, workspace, code->sm_count, static_cast<const int8_t*>(llr),
                                    n_frames, params->max_iter, params->early_stop, hard_bits, iters_used,
                                    syndrome_ok, static_cast<int16_t*>(llr_out), st);
+  } else if (ch.kind == Choice::PINGPONG_INT8) {
+    err = ldpc::pingpong_int8_decode(v, r, form, ch.pingpong, workspace, static_cast<const int8_t*>(llr), n_frames,
+                                     params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
+                                     static_cast<int16_t*>(llr_out), st);
   } else if (ch.kind == Choice::PERSIST_INT8) {
     err = ldpc::persist_int8_decode(v, r, form, ch.persist, workspace, code->sm_count,
                                     static_cast<const int8_t*>(llr), n_frames, params->max_iter, params->early_stop,

@@ -1,0 +1,462 @@
+// pingpong.cu -- single-scan min-sum (Section IV Eq. (3); Section V) with the
+// frame state in device memory, one kernel launch per iteration and no column
+// pass, for codes whose checks all have degree <= 8.
+//
+// Workspace (lane unit = frame pair, FP pairs, a multiple of 64; a warp lane
+// takes two neighbouring pairs, so a warp covers 64 pairs = 128 frames):
+//   zb [2][N][FP] half2  two posterior buffers.  Iteration k reads Z^(k-1) from
+//                        zb[(k-1)&1] and adds L^(k) - L^(k-2) into zb[k&1], which
+//                        holds Z^(k-2): afterwards zb[k&1] holds Z^(k).  Both
+//                        buffers start at Z^(0) = q0, with L^(0) = L^(-1) = 0.  The
+//                        adds are f16x2 atomics (two pairs per 8-byte add).  Every
+//                        partial sum is q0_n plus one message of each check of n
+//                        (of iteration k or k-2), an integer of magnitude <= 128 +
+//                        d_v Qm < 2048, which binary16 holds exactly: the sums are
+//                        exact and do not depend on the order of the atomics.
+//   st [2][rows][FP]     Section V state of iterations k-1 and k-2 in 8 bytes per
+//                        pair (A, B, n~, signs; rows = M), or per-edge bytes L +
+//                        128 (u16 per pair, rows = ell_w M edge slots);
+//                        iteration k reads both and overwrites the older.
+//   act/fail [3][FP]     bit masks per pair: frames running at iteration j, and
+//                        frames whose decisions x^(j-1) fail a check (found by
+//                        iteration j), at index j mod 3.
+//   iters [2 FP], okw [FP].
+//
+// Kernels per decode: init (channel values to both buffers, flags), one row
+// kernel per iteration, the final syndrome, the output.  The row kernel of
+// iteration k finds the parity of x^(k-1); that of k+1 stops the frames whose
+// x^(k-1) satisfied H (Section III's stop rule, also checked before the first
+// iteration): their result Z^(k-1) is in zb[(k-1)&1], and they are masked out
+// of every later atomic.
+#include <algorithm>
+
+#include "h2_body.cuh"
+#include "kernels.h"
+#include "pp_check.cuh"
+
+namespace ldpc {
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int kWarps = 8;   // per block
+constexpr int kRows = 4;    // checks per warp
+constexpr int kTile = kWarps * kRows;
+
+__host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct PP2 {
+  uint32_t* zb;    // [2][N][FP]
+  char* st;        // [2][rows][FP] units of ub bytes
+  uint32_t* act;   // [3][FP]
+  uint32_t* fail;  // [3][FP]
+  int32_t* iters;  // [2 FP]
+  uint32_t* okw;   // [FP]
+  int32_t F, FP, rows, ub;
+};
+
+__device__ __forceinline__ uint32_t half_mask(uint32_t b) {
+  return ((b & 1u) ? 0x0000ffffu : 0u) | ((b & 2u) ? 0xffff0000u : 0u);
+}
+__device__ __forceinline__ uint32_t valid_bits(int p, int F) {
+  return (2 * p < F ? 1u : 0u) | (2 * p + 1 < F ? 2u : 0u);
+}
+
+// 8-byte f16x2 atomic add of two frame pairs (no result).
+__device__ __forceinline__ void red_add_h2x2(uint32_t* p, uint32_t a, uint32_t b) {
+  asm volatile("red.global.add.noftz.v2.f16x2 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b) : "memory");
+}
+
+// L^(k)_j - L^(k-2)_j for successive positions j of one check and frame pair.
+struct Delta {
+  uint32_t An, Dn, In, SN;  // iteration k: A, B - A, n~, signs (shifted as j advances)
+  uint32_t Ao, Do, Io, SO;  // iteration k-2
+  __device__ __forceinline__ Delta(const NewState& n, const SV& o)
+      : An(n.An), Dn(hsub(n.Bn, n.An)), In(n.In), SN(n.Sn), Ao(o.A), Do(hsub(o.B, o.A)), Io(o.I), SO(o.S) {}
+  __device__ __forceinline__ uint32_t next(int j) {
+    const uint32_t Ln = hfma(Dn, heq_one(In, h2c(j)), An) ^ (SN & 0x80008000u);
+    const uint32_t Lo = hfma(Do, heq_one(Io, h2c(j)), Ao) ^ (SO & 0x80008000u);
+    SN += SN;
+    SO += SO;
+    return hsub(Ln, Lo);
+  }
+};
+
+__device__ __forceinline__ uint2 pack_c8(const NewState& n) {
+  return make_uint2((uint32_t)n.al | ((uint32_t)n.ah << 8) | ((uint32_t)n.bl << 16) | ((uint32_t)n.bh << 24),
+                    (uint32_t)n.il | ((uint32_t)n.ih << 16) | (n.Sn & 0xff00ff00u));
+}
+
+struct RowArgs {
+  const uint32_t* Zr;  // Z^(k-1) at the lane's first pair
+  uint32_t* Za;        // Z^(k-2) -> Z^(k), at the lane's first pair
+  const char* S1;      // state of k-1 at the lane's first pair (bytes)
+  char* S2;            // state of k-2, overwritten with k
+  uint32_t FP, M;
+  uint32_t amA, amB;   // running halves of the lane's two pairs
+  uint32_t ksat;
+  H2Rule rule;
+};
+
+// One check m of degree d (D > 0: exactly D) for the lane's two pairs, handles
+// h[j] (variable x FP).  Returns the decision parities of x^(k-1) of both pairs
+// (bits 0-1 first pair, 2-3 second).
+template <int FORM, bool ES, int D>
+__device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const uint32_t* h) {
+  constexpr int NJ = D > 0 ? D : 8;
+  uint32_t wa[NJ], wb[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      const uint2 v = __ldcg(reinterpret_cast<const uint2*>(x.Zr + h[j]));
+      wa[j] = v.x;
+      wb[j] = v.y;
+    }
+  }
+  uint32_t pa = 0, pb = 0;
+  if constexpr (FORM == 1) {
+    const size_t so = (size_t)m * x.FP * 8;
+    const uint4 s1 = __ldcg(reinterpret_cast<const uint4*>(x.S1 + so));
+    const uint4 s2 = __ldcg(reinterpret_cast<const uint4*>(x.S2 + so));
+    const NewState na = sv_pass1<D, 8, ES>(wa, d, SVUnit<true>::unpack(make_uint2(s1.x, s1.y)), x.rule, x.ksat, pa);
+    const NewState nb = sv_pass1<D, 8, ES>(wb, d, SVUnit<true>::unpack(make_uint2(s1.z, s1.w)), x.rule, x.ksat, pb);
+    Delta ga(na, SVUnit<true>::unpack(make_uint2(s2.x, s2.y)));
+    Delta gb(nb, SVUnit<true>::unpack(make_uint2(s2.z, s2.w)));
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (D > 0 || j < d) {
+        const uint32_t da = ga.next(j) & x.amA, db = gb.next(j) & x.amB;
+        if ((x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
+      }
+    }
+    const uint2 ua = pack_c8(na), ub = pack_c8(nb);
+    __stcg(reinterpret_cast<uint4*>(x.S2 + so), make_uint4(ua.x, ua.y, ub.x, ub.y));
+  } else {
+    // per-edge: slot j M + m holds the byte pairs of both pairs in one word
+    uint32_t l1[NJ], l2[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (D > 0 || j < d) {
+        const size_t so = (size_t)(j * x.M + m) * x.FP * 2;
+        l1[j] = __ldcg(reinterpret_cast<const uint32_t*>(x.S1 + so));
+        l2[j] = __ldcg(reinterpret_cast<const uint32_t*>(x.S2 + so));
+      }
+    }
+    uint32_t K1a = x.ksat, K2a = x.ksat, NEGa = 0, Ya = 0, K1b = x.ksat, K2b = x.ksat, NEGb = 0, Yb = 0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (D > 0 || j < d) {
+        key_step(hsub(wa[j], pe_to_h2(l1[j] & 0xffffu)), j, K1a, K2a, NEGa);
+        key_step(hsub(wb[j], pe_to_h2(l1[j] >> 16)), j, K1b, K2b, NEGb);
+        if (ES) {
+          Ya ^= dec_bits(wa[j]);
+          Yb ^= dec_bits(wb[j]);
+        }
+      }
+    }
+    const int dd = D > 0 ? D : d;
+    const NewState na = finish_state(K1a, K2a, NEGa, dd, x.rule), nb = finish_state(K1b, K2b, NEGb, dd, x.rule);
+    const uint32_t Dna = hsub(na.Bn, na.An), Dnb = hsub(nb.Bn, nb.An);
+    uint32_t SNa = na.Sn, SNb = nb.Sn;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (D > 0 || j < d) {
+        const uint32_t La = hfma(Dna, heq_one(na.In, h2c(j)), na.An) ^ (SNa & 0x80008000u);
+        const uint32_t Lb = hfma(Dnb, heq_one(nb.In, h2c(j)), nb.An) ^ (SNb & 0x80008000u);
+        SNa += SNa;
+        SNb += SNb;
+        const uint32_t da = hsub(La, pe_to_h2(l2[j] & 0xffffu)) & x.amA;
+        const uint32_t db = hsub(Lb, pe_to_h2(l2[j] >> 16)) & x.amB;
+        if ((x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
+        __stcg(reinterpret_cast<uint32_t*>(x.S2 + (size_t)(j * x.M + m) * x.FP * 2), h2_to_pe(La) | (h2_to_pe(Lb) << 16));
+      }
+    }
+    if (ES) {
+      pa = ((Ya >> 15) & 1u) | ((Ya >> 30) & 2u);
+      pb = ((Yb >> 15) & 1u) | ((Yb >> 30) & 2u);
+    }
+  }
+  return pa | (pb << 2);
+}
+
+// Row kernel of iteration k: block (bx, chunk) takes kTile checks of the
+// degree-sorted order for the chunk's 64 pairs (warp w: checks bx kTile + w kRows
+// ..., lane l: pairs chunk 64 + 2 l, + 1).
+template <int FORM, bool ES>
+__global__ void __launch_bounds__(kWarps * 32, 3) pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.y * 64 + 2 * lane;
+  const int FP = s.FP;
+  uint32_t aA = valid_bits(p, s.F), aB = valid_bits(p + 1, s.F);
+  if (ES) {
+    const int pb = (k - 1) % 3;
+    const uint2 a = *reinterpret_cast<const uint2*>(s.act + pb * FP + p);
+    const uint2 f = *reinterpret_cast<const uint2*>(s.fail + pb * FP + p);
+    aA = a.x & f.x;
+    aB = a.y & f.y;
+    if (blockIdx.x == 0 && warp == 0) {
+      // frames whose x^(k-2) satisfied H stop with k - 2 iterations
+      const uint32_t st[2] = {a.x & ~f.x, a.y & ~f.y};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (st[q] & 1u) s.iters[2 * (p + q)] = k - 2;
+        if (st[q] & 2u) s.iters[2 * (p + q) + 1] = k - 2;
+        if (st[q]) s.okw[p + q] |= st[q];
+      }
+      *reinterpret_cast<uint2*>(s.act + (k % 3) * FP + p) = make_uint2(aA, aB);
+      *reinterpret_cast<uint2*>(s.fail + ((k + 1) % 3) * FP + p) = make_uint2(0u, 0u);
+    }
+  }
+  if (__all_sync(kFull, (aA | aB) == 0u)) return;
+  RowArgs x;
+  const size_t nfp = (size_t)c.N * FP, sfp = (size_t)s.rows * FP * s.ub;
+  x.Zr = s.zb + (size_t)((k - 1) & 1) * nfp + p;
+  x.Za = s.zb + (size_t)(k & 1) * nfp + p;
+  x.S1 = s.st + (size_t)((k - 1) & 1) * sfp + (size_t)p * s.ub;
+  x.S2 = s.st + (size_t)(k & 1) * sfp + (size_t)p * s.ub;
+  x.FP = (uint32_t)FP;
+  x.M = (uint32_t)c.M;
+  x.amA = half_mask(aA);
+  x.amB = half_mask(aB);
+  x.rule = make_h2rule(ir);
+  // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
+  x.ksat = hfma(ints_to_h2(ir.qm, ir.qm), h2c_q11(16), h2c_q11(15));
+  const int m0 = blockIdx.x * kTile + warp * kRows;
+  const int nr = min(kRows, c.M - m0);
+  if (nr <= 0) return;
+  uint32_t fail = 0;
+  const int d0 = c.deg(m0);
+  if (nr == kRows && d0 == c.deg(m0 + nr - 1) && (d0 == 6 || d0 == 7)) {
+    // lane l < kRows d0 holds the handle of (check m0 + l / d0, position l % d0)
+    uint32_t hl = 0;
+    if (lane < kRows * d0) {
+      const int r = lane / d0, j = lane - r * d0;
+      hl = (uint32_t)c.col(j, m0 + r) * x.FP;
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      uint32_t h[8];
+      if (d0 == 6) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) h[j] = __shfl_sync(kFull, hl, r * 6 + j);
+        fail |= check2<FORM, ES, 6>(x, m0 + r, 6, h);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 7; ++j) h[j] = __shfl_sync(kFull, hl, r * 7 + j);
+        fail |= check2<FORM, ES, 7>(x, m0 + r, 7, h);
+      }
+    }
+  } else {
+    for (int r = 0; r < nr; ++r) {
+      const int m = m0 + r, d = c.deg(m);
+      uint32_t h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j < d) h[j] = (uint32_t)c.col(j, m) * x.FP;
+      fail |= check2<FORM, ES, 0>(x, m, d, h);
+    }
+  }
+  if (ES) {
+    const uint32_t fa = fail & 3u & aA, fb = (fail >> 2) & aB;
+    if (fa) atomicOr(s.fail + (k % 3) * FP + p, fa);
+    if (fb) atomicOr(s.fail + (k % 3) * FP + p + 1, fb);
+  }
+}
+
+// Channel values (frame-major int8) into both posterior buffers as binary16
+// pairs; flags.  Tile: 64 variables x 32 pairs.
+template <bool ES>
+__global__ void __launch_bounds__(256) pp2_init(const DevCode c, const int8_t* __restrict__ llr, PP2 s, int K) {
+  __shared__ int8_t tile[64][65];  // [frame][variable]
+  const int n0 = blockIdx.x * 64, p0 = blockIdx.y * 32;
+  const int N = c.N, F = s.F, FP = s.FP;
+  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+    const int fl = i >> 6, nl = i & 63;
+    const int f = 2 * p0 + fl, n = n0 + nl;
+    tile[fl][nl] = (f < F && n < N) ? llr[(size_t)f * N + n] : (int8_t)0;
+  }
+  __syncthreads();
+  const size_t nfp = (size_t)N * FP;
+  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+    const int nl = i >> 5, pl = i & 31;
+    const int n = n0 + nl, p = p0 + pl;
+    if (n >= N) continue;
+    const uint32_t hz = ints_to_h2(tile[2 * pl][nl], tile[2 * pl + 1][nl]);
+    const size_t o = (size_t)n * FP + p;
+    s.zb[o] = hz;
+    s.zb[nfp + o] = hz;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    const int p = p0 + threadIdx.x;
+    s.act[p] = valid_bits(p, F);
+    s.fail[p] = ES ? kFull : 0u;  // "x^(-1) failed": every valid frame runs iteration 1
+    s.fail[FP + p] = 0u;
+    s.fail[2 * FP + p] = 0u;
+    s.iters[2 * p] = K;
+    s.iters[2 * p + 1] = K;
+    s.okw[p] = 0u;
+  }
+}
+
+// Syndrome of x^(K) for the frames still running; frames whose x^(K-1) satisfied
+// H stop with K - 1 iterations.
+template <bool ES>
+__global__ void __launch_bounds__(kWarps * 32) pp2_final(const DevCode c, PP2 s, int K) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.y * 64 + 2 * lane;
+  const int FP = s.FP;
+  uint32_t aA = valid_bits(p, s.F), aB = valid_bits(p + 1, s.F);
+  if (ES) {
+    const int pb = K % 3;
+    const uint2 a = *reinterpret_cast<const uint2*>(s.act + pb * FP + p);
+    const uint2 f = *reinterpret_cast<const uint2*>(s.fail + pb * FP + p);
+    aA = a.x & f.x;
+    aB = a.y & f.y;
+    if (blockIdx.x == 0 && warp == 0) {
+      const uint32_t st[2] = {a.x & ~f.x, a.y & ~f.y};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (st[q] & 1u) s.iters[2 * (p + q)] = K - 1;
+        if (st[q] & 2u) s.iters[2 * (p + q) + 1] = K - 1;
+        if (st[q]) s.okw[p + q] |= st[q];
+      }
+    }
+  }
+  if (blockIdx.x == 0 && warp == 0) *reinterpret_cast<uint2*>(s.act + ((K + 1) % 3) * FP + p) = make_uint2(aA, aB);
+  if (__all_sync(kFull, (aA | aB) == 0u)) return;
+  const uint32_t* Zk = s.zb + (size_t)(K & 1) * c.N * FP + p;
+  const int m0 = blockIdx.x * kTile + warp * kRows;
+  const int m1 = min(m0 + kRows, c.M);
+  uint32_t fa = 0, fb = 0;
+  for (int m = m0; m < m1; ++m) {
+    const int d = c.deg(m);
+    uint32_t ya = 0, yb = 0;
+    for (int j = 0; j < d; ++j) {
+      const uint2 v = *reinterpret_cast<const uint2*>(Zk + (size_t)c.col(j, m) * FP);
+      ya ^= dec_bits(v.x);
+      yb ^= dec_bits(v.y);
+    }
+    fa |= ((ya >> 15) & 1u) | ((ya >> 30) & 2u);
+    fb |= ((yb >> 15) & 1u) | ((yb >> 30) & 2u);
+  }
+  fa &= aA;
+  fb &= aB;
+  if (fa) atomicOr(s.fail + ((K + 1) % 3) * FP + p, fa);
+  if (fb) atomicOr(s.fail + ((K + 1) % 3) * FP + p + 1, fb);
+}
+
+// Frame-major outputs through a 64-variable x 32-pair tile; each frame's result
+// is the buffer of its iteration count.
+__global__ void __launch_bounds__(256) pp2_output(const DevCode c, PP2 s, int K, uint8_t* bits, int32_t* iters,
+                                                  uint8_t* okf, int16_t* zout) {
+  __shared__ uint32_t tile[64][33];  // [variable][pair]
+  const int n0 = blockIdx.x * 64, p0 = blockIdx.y * 32;
+  const int N = c.N, N8 = (N + 7) >> 3, FP = s.FP, F = s.F;
+  const size_t nfp = (size_t)N * FP;
+  const int pl = threadIdx.x & 31, p = p0 + pl;
+  const uint32_t* zl = s.zb + (size_t)(s.iters[2 * p] & 1) * nfp + p;
+  const uint32_t* zh = s.zb + (size_t)(s.iters[2 * p + 1] & 1) * nfp + p;
+  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+    const int nl = i >> 5;
+    const int n = n0 + nl;
+    uint32_t v = 0;
+    if (n < N) {
+      const uint32_t a = zl[(size_t)n * FP];
+      v = (zl == zh) ? a : ((a & 0xffffu) | (zh[(size_t)n * FP] & 0xffff0000u));
+    }
+    tile[nl][pl] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 64 * 8; i += blockDim.x) {
+    const int fl = i >> 3, bl = i & 7;
+    const int f = 2 * p0 + fl, b = (n0 >> 3) + bl;
+    if (f >= F || b >= N8) continue;
+    uint32_t byte = 0;
+    for (int t = 0; t < 8; ++t) {
+      const int nl = bl * 8 + t;
+      if (n0 + nl < N) byte |= ((dec_bits(tile[nl][fl >> 1] >> (16 * (fl & 1))) >> 15) & 1u) << t;
+    }
+    bits[(size_t)f * N8 + b] = (uint8_t)byte;
+  }
+  if (zout != nullptr) {
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+      const int fl = i >> 6, nl = i & 63;
+      const int f = 2 * p0 + fl, n = n0 + nl;
+      if (f >= F || n >= N) continue;
+      const uint32_t hz = tile[nl][fl >> 1];
+      zout[(size_t)f * N + n] = (int16_t)((fl & 1) ? h_hi_int(hz) : h_lo_int(hz));
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 64) {
+    const int f = 2 * p0 + threadIdx.x;
+    if (f < F) {
+      const int pp = f >> 1, b = f & 1, kb = (K + 1) % 3;
+      const uint32_t a = s.act[kb * FP + pp], fl = s.fail[kb * FP + pp];
+      iters[f] = s.iters[f];
+      okf[f] = ((a >> b) & 1u) ? (uint8_t)(((fl >> b) & 1u) ^ 1u) : (uint8_t)((s.okw[pp] >> b) & 1u);
+    }
+  }
+}
+
+template <int FORM, bool ES>
+cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, const int8_t* llr, int K, uint8_t* bits,
+                    int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
+  const dim3 tgrid((unsigned)((c.N + 63) / 64), (unsigned)(s.FP / 32));
+  const dim3 rgrid((unsigned)((c.M + kTile - 1) / kTile), (unsigned)(s.FP / 64));
+  pp2_init<ES><<<tgrid, 256, 0, st>>>(c, llr, s, K);
+  for (int k = 1; k <= K; ++k) pp2_rows<FORM, ES><<<rgrid, kWarps * 32, 0, st>>>(c, r, s, k);
+  pp2_final<ES><<<rgrid, kWarps * 32, 0, st>>>(c, s, K);
+  pp2_output<<<tgrid, 256, 0, st>>>(c, s, K, bits, iters, ok, zout);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+PingpongLayout pingpong_layout(int form, int N, int M, int ell_w, int F) {
+  PingpongLayout L;
+  L.lanes = (((F + 1) / 2) + 63) / 64 * 64;
+  L.ub = form == 1 ? 8 : 2;
+  L.rows = form == 1 ? M : ell_w * M;
+  const size_t lanes = (size_t)L.lanes;
+  size_t off = 0;
+  L.zb = off;    off = al256(off + 2 * (size_t)N * lanes * 4);
+  L.st = off;    off = al256(off + 2 * (size_t)L.rows * lanes * L.ub);
+  L.act = off;   off = al256(off + 3 * lanes * 4);
+  L.fail = off;  off = al256(off + 3 * lanes * 4);
+  L.iters = off; off = al256(off + 2 * lanes * 4);
+  L.ok = off;    off = al256(off + lanes * 4);
+  L.total = off;
+  return L;
+}
+
+bool pingpong_int8_eligible(int N, int M, int ell_w, int max_row_deg, int max_col_deg, int qm, int form, int F) {
+  if (max_row_deg > 8 || 128 + (int64_t)(max_col_deg + 1) * qm > 2048) return false;
+  const PingpongLayout L = pingpong_layout(form, N, M, ell_w, F);
+  // element offsets within one buffer fit 32 bits
+  return (uint64_t)N * L.lanes < (1ull << 32) && (uint64_t)L.rows * L.lanes < (1ull << 32);
+}
+
+cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, const PingpongLayout& L, void* ws,
+                                 const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
+                                 int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
+  char* b = static_cast<char*>(ws);
+  PP2 s;
+  s.zb = reinterpret_cast<uint32_t*>(b + L.zb);
+  s.st = b + L.st;
+  s.act = reinterpret_cast<uint32_t*>(b + L.act);
+  s.fail = reinterpret_cast<uint32_t*>(b + L.fail);
+  s.iters = reinterpret_cast<int32_t*>(b + L.iters);
+  s.okw = reinterpret_cast<uint32_t*>(b + L.ok);
+  s.F = F;
+  s.FP = L.lanes;
+  s.rows = L.rows;
+  s.ub = L.ub;
+  // L^(0) = L^(-1) = 0: Section V state all zero, per-edge bytes L + 128 = 0x80
+  cudaError_t e = cudaMemsetAsync(b + L.st, form == 1 ? 0 : 0x80, L.act - L.st, st);
+  if (e != cudaSuccess) return e;
+  if (form == 1) return early_stop ? pp2_run<1, true>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
+                                   : pp2_run<1, false>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
+  return early_stop ? pp2_run<0, true>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
+                    : pp2_run<0, false>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
+}
+
+}  // namespace ldpc

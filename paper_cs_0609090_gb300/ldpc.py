@@ -29,11 +29,12 @@ FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan
 RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED,
          "sum_product": LDPC_RULE_SUM_PRODUCT}
 (LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM, LDPC_KERNEL_CLUSTER,
- LDPC_KERNEL_PERSISTENT) = range(6)
+ LDPC_KERNEL_PERSISTENT, LDPC_KERNEL_PINGPONG) = range(7)
 LDPC_SCHEDULE_FLOODING, LDPC_SCHEDULE_LAYERED = 0, 1
 SCHEDULES = {"flooding": LDPC_SCHEDULE_FLOODING, "layered": LDPC_SCHEDULE_LAYERED}
 KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF,
-           "stream": LDPC_KERNEL_STREAM, "cluster": LDPC_KERNEL_CLUSTER, "persistent": LDPC_KERNEL_PERSISTENT}
+           "stream": LDPC_KERNEL_STREAM, "cluster": LDPC_KERNEL_CLUSTER, "persistent": LDPC_KERNEL_PERSISTENT,
+           "pingpong": LDPC_KERNEL_PINGPONG}
 
 # Every symbol include/ldpc_gb300.h declares.
 EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_workspace_size",

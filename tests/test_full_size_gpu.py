@@ -29,14 +29,14 @@ def _sample(F, k, seed):
 @pytest.mark.parametrize("form", FORMS_INT)
 def test_irr_64800_full_batch_sampled(L, form):
     """1024 frames, 50 iterations, early stop off: the library's choice (as
-    bench.py times it) and the persistent streaming kernel, sampled frames
-    against the oracle."""
+    bench.py times it), the two-launch and the persistent streaming kernels,
+    sampled frames against the oracle."""
     w = I.make_workload("irr_n64800")
     p = dict(w.params, early_stop=0)
     h = L.Code.from_inputs(w.code)
     frames = _sample(w.n_frames, 3, 1)
     o = oracle_int(w.code, w.q0[frames], form, p)
-    for kern in ("auto", "persistent"):
+    for kern in ("auto", "stream", "persistent"):
         g = gpu_decode(h, w.code.n_vars, w.q0, L.make_params(form=form, kernel=kern, **p))
         assert_int_parity({k: v[frames] for k, v in g.items()}, o)
 
@@ -97,7 +97,7 @@ def test_zero_frames_is_a_noop(L):
     it = torch.full((2,), -7, dtype=torch.int32, device="cuda")
     ok = torch.full((2,), 9, dtype=torch.uint8, device="cuda")
     q = torch.from_numpy(w.q0).cuda()
-    for kern in ("auto", "onchip_int", "stream", "cluster", "persistent"):
+    for kern in ("auto", "onchip_int", "stream", "cluster", "persistent", "pingpong"):
         p = L.make_params(kernel=kern, **w.params)
         assert L.ldpc_workspace_size(h.handle, p, 0) == 0
         L.ldpc_decode_batch(h.handle, p, q, 0, bits, it, ok)

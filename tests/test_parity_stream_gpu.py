@@ -37,7 +37,7 @@ def _int(L, code, q0, form, p, kernel="stream"):
     return g
 
 
-STREAM_KERNELS = ("stream", "persistent")
+STREAM_KERNELS = ("stream", "persistent", "pingpong")
 
 
 @pytest.mark.parametrize("kernel", STREAM_KERNELS)
@@ -50,6 +50,11 @@ def test_int8_stream_small_codes(L, form, early_stop, kernel):
     w = I.make_workload("reg36_n1008", n_frames=301, ebn0_db=1.8)
     _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop), kernel=kernel)
     w = I.make_workload("qc_n7493", n_frames=67, ebn0_db=2.0)
+    if kernel == "pingpong":  # checks of degree 14 and 15: the ping-pong kernel takes degree <= 8
+        h = L.Code.from_inputs(w.code)
+        with pytest.raises(L.LdpcError):
+            L.ldpc_workspace_size(h.handle, L.make_params(form=form, kernel=kernel, **w.params), 67)
+        return
     _int(L, w.code, w.q0, form, dict(w.params, early_stop=early_stop), kernel=kernel)
 
 
@@ -69,14 +74,14 @@ def test_int8_stream_edge_cases(L, form, kernel):
 @pytest.mark.parametrize("form", FORMS_INT)
 @pytest.mark.parametrize("early_stop", [1, 0])
 def test_int8_irregular_64800(L, form, early_stop):
-    """The N=64800 code does not fit one SM: the two-launch streaming kernel (the
-    library's choice), the persistent streaming kernel and the cluster kernel
-    (8 CTAs, distributed shared memory) all decode it."""
+    """The N=64800 code does not fit one SM: the ping-pong kernel (the library's
+    choice), the two-launch streaming kernel, the persistent kernel and the
+    cluster kernel (8 CTAs, distributed shared memory) all decode it."""
     w = I.make_workload("irr_n64800", n_frames=7, frame_seed=3)
     p = dict(w.params, early_stop=early_stop)
     h = L.Code.from_inputs(w.code)
     assert L.ldpc_workspace_size(h.handle, L.make_params(form=form, **p), 7) > 0
-    for kern in ("auto", "persistent", "stream", "cluster"):
+    for kern in ("auto", "pingpong", "persistent", "stream", "cluster"):
         _int(L, w.code, w.q0, form, p, kernel=kern)
         if early_stop:
             q = I.noiseless(w.codewords[:2], 127)
