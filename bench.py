@@ -59,7 +59,11 @@ def algorithmic_bytes(code, form: str, iters: int, frames: int, dtype: str = "in
         s_l = (4 if f32 else 1) * E
     else:  # two-scan: Z_mn and L_mn cells read and written, plus q0 and decisions
         s_l = None
-    if s_l is None:
+    if form == "two_scan_1bit":
+        # two-scan with the Section V message storage: Z_mn read and written per
+        # edge, the state written and read once, q0 and decisions
+        b_it = 2 * E + 2 * ((dmax + 7) // 8 + 3) * M + N + N // 8
+    elif s_l is None:
         b_it = (4 if not f32 else 16) * E + N + N // 8
     else:
         b_it = 2 * b_z * N + 2 * s_l
@@ -127,6 +131,7 @@ def measured_peaks() -> dict:
 
 
 KERNEL_SOURCES = {"onchip_h2_kernel": "onchip_h2.cu", "onchip_int8_kernel": "onchip_int8.cu", "pp_kernel": "persist.cu", "pp2_rows": "pingpong.cu",
+                  "ts_horizontal": "twoscan_stream.cu",
                   "onchip_twoscan_kernel": "onchip_twoscan.cu", "h2s_rows": "stream.cu", "f32s_rows": "stream_f32.cu",
                   "layered_kernel": "layered_h2.cu"}
 
@@ -225,6 +230,22 @@ def roofline_line(kname, w, form, dtype, F, ms_step, clocks, sm_count):
             "kernel": kname, "kernel_ms": ms_step,
             "hbm_effective": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "peak_source",
                                                  "algorithmic_bytes_per_launch", "bytes_per_frame_iter")}}
+
+
+def kernel_name(form: str, dtype: str, schedule: str, chosen: str, ws_bytes: int, code) -> str:
+    """The kernel that dominates a decode of this request (the one the roofline
+    line describes)."""
+    if schedule == "layered":
+        return "layered_kernel"
+    if form in ("two_scan", "two_scan_1bit"):
+        return "ts_horizontal" if ws_bytes > 0 else "onchip_twoscan_kernel"
+    named = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel", "cluster": "multi_h2_kernel",
+             "persistent": "pp_kernel", "pingpong": "pp2_rows"}
+    if chosen in named:
+        return named[chosen]
+    if chosen == "stream":
+        return "f32s_rows" if dtype == "f32" else "h2s_rows"
+    return "onchip_h2_kernel"
 
 
 def cpu_oracle_sample(w, form: str, budget_s: float, max_frames: int, layers=None):
@@ -620,7 +641,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="qc_n7493")
-    ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan"])
+    ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan", "two_scan_1bit"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto",
                     choices=["auto", "onchip_int", "onchip_half", "stream", "cluster", "persistent", "pingpong"])
@@ -665,20 +686,7 @@ def main():
     params = ldpc.make_params(form=args.form, kernel=args.kernel, schedule=args.schedule, **wp)
     ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
     chosen = ldpc.ldpc_kernel_choice(code.handle, params, F)
-    kname = {"onchip_int": "onchip_int8_kernel", "onchip_half": "onchip_h2_kernel",
-             "cluster": "multi_h2_kernel", "persistent": "pp_kernel", "pingpong": "pp2_rows"}.get(
-                 chosen if args.kernel == "auto" else args.kernel)
-    if args.schedule == "layered":
-        kname = "layered_kernel"
-    elif kname is None and ws_bytes > 0:
-        kname = "f32s_rows" if args.dtype == "f32" else "h2s_rows"
-    elif args.form == "two_scan":
-        kname = "onchip_twoscan_kernel"
-    elif kname is None:
-        info = ldpc.ldpc_code_info(code.handle)
-        half_ok = info["max_row_degree"] <= 16 and \
-            128 + (info["max_col_degree"] + 1) * w.params["msg_sat"] <= 2048
-        kname = "onchip_h2_kernel" if half_ok else "onchip_int8_kernel"
+    kname = kernel_name(args.form, args.dtype, args.schedule, chosen, ws_bytes, code)
     host_llr = w.q0 if args.dtype == "int8" else w.llr.astype(np.float32)
     llr = torch.from_numpy(host_llr).to(dev)
     bits = torch.empty((F, (N + 7) // 8), dtype=torch.uint8, device=dev)

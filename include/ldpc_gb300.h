@@ -12,7 +12,10 @@
  *   - Section V, Eqs. (4)-(5): the single scan whose persistent state per check
  *     is (A_m, B_m, n~_m) and one sign bit per edge (LDPC_FORM_SS_1BIT);
  *   - Section III, Eqs. (1)-(2) literally (horizontal then vertical scan), as a
- *     comparator (LDPC_FORM_TWO_SCAN).
+ *     comparator (LDPC_FORM_TWO_SCAN), and the same two-scan algorithm with its
+ *     check messages stored in the Section V form (A_m, B_m, n~_m and one sign
+ *     bit per edge; Section V notes that the storage applies to the original
+ *     algorithm too): LDPC_FORM_TWO_SCAN_1BIT.
  *
  * Conventions shared by every entry point:
  *   - Every call returns an ldpc_status; nothing is thrown across the ABI.  On
@@ -57,13 +60,16 @@ typedef int32_t ldpc_status;
 typedef struct ldpc_code ldpc_code;
 
 enum { LDPC_DTYPE_INT8 = 0, LDPC_DTYPE_F32 = 1 };
-enum { LDPC_FORM_SS_FIXED = 0, LDPC_FORM_SS_1BIT = 1, LDPC_FORM_TWO_SCAN = 2 };
+enum { LDPC_FORM_SS_FIXED = 0, LDPC_FORM_SS_1BIT = 1, LDPC_FORM_TWO_SCAN = 2, LDPC_FORM_TWO_SCAN_1BIT = 3 };
 enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2, LDPC_RULE_SUM_PRODUCT = 3 };
 
 /* Decoder settings (Section III: lambda_k, beta_k constant over k; cap).
  *   dtype      LDPC_DTYPE_INT8: llr is int8, messages are integers saturated to
  *              msg_sat; LDPC_DTYPE_F32: llr is float32.
- *   form       which of the three algorithms above runs.
+ *   form       which of the four algorithms above runs.  The two-scan forms run
+ *              frame-resident (TWO_SCAN on codes whose edge cells fit one SM,
+ *              kernel AUTO or ONCHIP_HALF) or with the frame state in the
+ *              workspace (kernel AUTO or STREAM; row and column degree <= 16).
  *   rule       PLAIN; OFFSET: |L| <- max(|L| - beta, 0); NORMALIZED: |L| <- lambda |L|;
  *              SUM_PRODUCT: the log-domain sum-product check rule that min-sum
  *              approximates (Section I), as an accuracy reference: L_mn = prod of

@@ -34,6 +34,7 @@ struct ldpc_code {
   uint8_t* d_rdeg = nullptr;
   int32_t* d_cptr = nullptr;
   int32_t* d_cslot = nullptr;
+  uint32_t* d_ccj = nullptr;
   int32_t n_classes = 0;
   int32_t class_deg[32] = {};       // check degree of each class, ascending
   int32_t ell_w = 0;

@@ -23,6 +23,9 @@ struct DevCode {
   // slots (j * M + m) of variable n are cslot[cptr[n] .. cptr[n+1]-1].
   const int32_t* __restrict__ cptr;   // [N+1]
   const int32_t* __restrict__ cslot;  // [E]
+  // The same edges as (internal check index) | (position j << 24) (the
+  // compressed two-scan's vertical scan); null when M >= 2^24.
+  const uint32_t* __restrict__ ccj;   // [E]
   // The internal order sorted by degree as runs: checks [dc_end[i-1], dc_end[i])
   // have degree dc_deg[i] (n_dc <= 4 runs; otherwise n_dc = 0 and rdeg serves).
   int32_t n_dc;

@@ -139,6 +139,21 @@ cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, c
                                  const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
                                  int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st);
 
+// The two-scan algorithm of Section III with the frame state in device memory
+// (twoscan_stream.cu), any code size: per-edge Z_mn, and the check messages per
+// edge (form2 0) or as the Section V state (form2 1).
+struct TwoScanLayout {
+  int lanes = 0;   // frame pairs, padded to 64
+  bool c8 = false; // compressed state in 8 bytes per pair (check degree <= 8), else 16
+  int ub = 0;
+  size_t zmn = 0, lmn = 0, st = 0, q0 = 0, zp = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
+};
+TwoScanLayout twoscan_layout(int form2, int N, int M, int ell_w, int F);
+bool twoscan_stream_eligible(int N, int M, int ell_w, int max_row_deg, int max_col_deg, int qm, int form2, int F);
+cudaError_t twoscan_stream_decode(const DevCode& c, const IntRule& r, int form2, const TwoScanLayout& L, void* ws,
+                                  const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
+                                  int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st);
+
 // The persistent streaming decoder (persist.cu): one kernel launch per decode,
 // a work queue over (chunk of 32 frame pairs, iteration, tile of checks) that
 // runs groups of W chunks through all their iterations while their state stays

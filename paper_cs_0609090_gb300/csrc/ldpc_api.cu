@@ -49,6 +49,7 @@ ldpc::DevCode view(const ldpc_code* c) {
   v.ell_w = c->ell_w;
   v.cptr = c->d_cptr;
   v.cslot = c->d_cslot;
+  v.ccj = c->d_ccj;
   v.n_dc = c->n_dc;
   for (int i = 0; i < 4; ++i) {
     v.dc_end[i] = c->dc_end[i];
@@ -115,7 +116,7 @@ ldpc_status set_layers(ldpc_code* c, int32_t n_layers, const int32_t* layer_of_c
 ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
   if (p->dtype != LDPC_DTYPE_INT8 && p->dtype != LDPC_DTYPE_F32)
     return fail(LDPC_ERR_INVALID_ARG, "dtype %d is not LDPC_DTYPE_INT8/F32", p->dtype);
-  if (p->form < LDPC_FORM_SS_FIXED || p->form > LDPC_FORM_TWO_SCAN)
+  if (p->form < LDPC_FORM_SS_FIXED || p->form > LDPC_FORM_TWO_SCAN_1BIT)
     return fail(LDPC_ERR_INVALID_ARG, "form %d is not a known LDPC_FORM_*", p->form);
   if (p->rule < LDPC_RULE_PLAIN || p->rule > LDPC_RULE_SUM_PRODUCT)
     return fail(LDPC_ERR_INVALID_ARG, "rule %d is not a known LDPC_RULE_*", p->rule);
@@ -168,11 +169,12 @@ constexpr int kPersistGroupChunks = LDPC_PP_GROUP_CHUNKS;
 // Which kernel serves a request; ws = workspace bytes it needs.
 struct Choice {
   enum Kind { NONE, ONCHIP_INT8, ONCHIP_H2, CLUSTER_H2, STREAM_INT8, PERSIST_INT8, PINGPONG_INT8, STREAM_F32,
-              ONCHIP_TWOSCAN, LAYERED } kind = NONE;
+              ONCHIP_TWOSCAN, STREAM_TWOSCAN, LAYERED } kind = NONE;
   ldpc::OnchipPlan onchip;
   ldpc::StreamLayout stream;
   ldpc::PersistLayout persist;
   ldpc::PingpongLayout pingpong;
+  ldpc::TwoScanLayout twoscan;
   ldpc::LayeredLayout layered;
   size_t ws = 0;
 };
@@ -240,17 +242,26 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
                 "cannot run on the requested frame-resident kernel (%d)",
                 c->N, c->M, c->E, c->max_row_deg, c->max_col_deg, p->kernel);
   }
-  if (p->dtype == LDPC_DTYPE_INT8 && p->form == LDPC_FORM_TWO_SCAN) {
-    if ((p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF) &&
+  if (p->dtype == LDPC_DTYPE_INT8 && (p->form == LDPC_FORM_TWO_SCAN || p->form == LDPC_FORM_TWO_SCAN_1BIT)) {
+    const int form2 = p->form == LDPC_FORM_TWO_SCAN_1BIT ? 1 : 0;
+    if (form2 == 0 && (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF) &&
         ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num) &&
         ldpc::onchip_twoscan_plan(v, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_TWOSCAN;
       ch->ws = 0;
       return LDPC_OK;
     }
-    return fail(LDPC_ERR_UNSUPPORTED, "the two-scan comparator needs a code whose edge cells fit one SM "
-                "(N=%d, E=%d) with row degree <= 16 and 128 + (max_col_degree + 1) * msg_sat <= 2048",
-                c->N, c->E);
+    if ((p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM) &&
+        (form2 == 0 || c->d_ccj != nullptr) &&
+        ldpc::twoscan_stream_eligible(c->N, c->M, c->ell_w, c->max_row_deg, c->max_col_deg, p->msg_sat, form2,
+                                      n_frames)) {
+      ch->kind = Choice::STREAM_TWOSCAN;
+      ch->twoscan = ldpc::twoscan_layout(form2, c->N, c->M, c->ell_w, n_frames);
+      ch->ws = ch->twoscan.total;
+      return LDPC_OK;
+    }
+    return fail(LDPC_ERR_UNSUPPORTED, "the two-scan decoders need row degree <= 16, column degree <= 16 and "
+                "128 + (max_col_degree + 1) * msg_sat <= 2048 (code N=%d, E=%d; kernel %d)", c->N, c->E, p->kernel);
   }
   if (p->dtype == LDPC_DTYPE_F32 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED) &&
       (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM)) {
@@ -325,11 +336,13 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   for (int32_t i = 0; i < n_checks; ++i) pos[(size_t)order[(size_t)i]] = i;
   // variable -> edge slots (j * M + internal check index), for the two-scan comparator
   std::vector<int32_t> cptr((size_t)n_vars + 1, 0), cslot((size_t)E), cfill((size_t)n_vars, 0);
+  std::vector<uint32_t> ccj((size_t)E);
   for (int32_t e = 0; e < E; ++e) cptr[(size_t)col_idx[e] + 1]++;
   for (int32_t n = 0; n < n_vars; ++n) cptr[(size_t)n + 1] += cptr[(size_t)n];
   for (int32_t m = 0; m < n_checks; ++m)
     for (int32_t j = 0; j < row_ptr[m + 1] - row_ptr[m]; ++j) {
       const int32_t n = col_idx[row_ptr[m] + j];
+      ccj[(size_t)(cptr[(size_t)n] + cfill[(size_t)n])] = (uint32_t)pos[(size_t)m] | ((uint32_t)j << 24);
       cslot[(size_t)(cptr[(size_t)n] + cfill[(size_t)n]++)] = j * n_checks + pos[(size_t)m];
     }
   for (int32_t i = 0; i < n_checks; ++i) {
@@ -386,6 +399,9 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
       (err = cudaMalloc(&c->d_cslot, sizeof(int32_t) * (size_t)E)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_cslot, cslot.data(), sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
+      (n_checks < (1 << 24) && (err = cudaMalloc(&c->d_ccj, sizeof(uint32_t) * (size_t)E)) != cudaSuccess) ||
+      (n_checks < (1 << 24) && (err = cudaMemcpy(c->d_ccj, ccj.data(), sizeof(uint32_t) * (size_t)E,
+                                                 cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (err = cudaMalloc(&c->d_rdeg, (size_t)n_checks)) != cudaSuccess ||
       (err = cudaMemcpy(c->d_rdeg, rdeg.data(), (size_t)n_checks, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (narrow && (err = cudaMalloc(&c->d_ell16, sizeof(uint16_t) * ell16.size())) != cudaSuccess) ||
@@ -405,6 +421,7 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
     cudaFree(c->d_ell32);
     cudaFree(c->d_cptr);
     cudaFree(c->d_cslot);
+    cudaFree(c->d_ccj);
     delete c;
     return cuda_fail(err, "ldpc_code_create device copy");
   }
@@ -455,6 +472,7 @@ ldpc_status ldpc_code_destroy(ldpc_code* code) {
   cudaFree(code->d_ell32);
   cudaFree(code->d_cptr);
   cudaFree(code->d_cslot);
+  cudaFree(code->d_ccj);
   cudaFree(code->d_lay_ptr);
   cudaFree(code->d_lay_rows);
   free_cluster_tables(code);
@@ -508,6 +526,7 @@ ldpc_status ldpc_kernel_choice(const ldpc_code* code, const ldpc_decode_params* 
     case Choice::ONCHIP_TWOSCAN: *kernel = LDPC_KERNEL_ONCHIP_HALF; break;
     case Choice::CLUSTER_H2: *kernel = LDPC_KERNEL_CLUSTER; break;
     case Choice::STREAM_INT8:
+    case Choice::STREAM_TWOSCAN:
     case Choice::STREAM_F32: *kernel = LDPC_KERNEL_STREAM; break;
     case Choice::PERSIST_INT8: *kernel = LDPC_KERNEL_PERSISTENT; break;
     case Choice::PINGPONG_INT8: *kernel = LDPC_KERNEL_PINGPONG; break;
@@ -567,6 +586,10 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
     err = ldpc::stream_int8_decode(v, r, form, ch.stream, workspace, code->sm_count, static_cast<const int8_t*>(llr),
                                    n_frames, params->max_iter, params->early_stop, hard_bits, iters_used,
                                    syndrome_ok, static_cast<int16_t*>(llr_out), st);
+  } else if (ch.kind == Choice::STREAM_TWOSCAN) {
+    err = ldpc::twoscan_stream_decode(v, r, params->form == LDPC_FORM_TWO_SCAN_1BIT ? 1 : 0, ch.twoscan, workspace,
+                                      static_cast<const int8_t*>(llr), n_frames, params->max_iter, params->early_stop,
+                                      hard_bits, iters_used, syndrome_ok, static_cast<int16_t*>(llr_out), st);
   } else if (ch.kind == Choice::PINGPONG_INT8) {
     err = ldpc::pingpong_int8_decode(v, r, form, ch.pingpong, workspace, static_cast<const int8_t*>(llr), n_frames,
                                      params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,

@@ -21,11 +21,12 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 LDPC_OK, LDPC_ERR_INVALID_ARG, LDPC_ERR_UNSUPPORTED, LDPC_ERR_CUDA, LDPC_ERR_OOM, LDPC_ERR_TIMEOUT = range(6)
 LDPC_DTYPE_INT8, LDPC_DTYPE_F32 = 0, 1
-LDPC_FORM_SS_FIXED, LDPC_FORM_SS_1BIT, LDPC_FORM_TWO_SCAN = 0, 1, 2
+LDPC_FORM_SS_FIXED, LDPC_FORM_SS_1BIT, LDPC_FORM_TWO_SCAN, LDPC_FORM_TWO_SCAN_1BIT = 0, 1, 2, 3
 LDPC_RULE_PLAIN, LDPC_RULE_OFFSET, LDPC_RULE_NORMALIZED, LDPC_RULE_SUM_PRODUCT = 0, 1, 2, 3
 
 DTYPES = {"int8": LDPC_DTYPE_INT8, "f32": LDPC_DTYPE_F32, "float32": LDPC_DTYPE_F32}
-FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN}
+FORMS = {"ss_fixed": LDPC_FORM_SS_FIXED, "ss_1bit": LDPC_FORM_SS_1BIT, "two_scan": LDPC_FORM_TWO_SCAN,
+         "two_scan_1bit": LDPC_FORM_TWO_SCAN_1BIT}
 RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDPC_RULE_NORMALIZED,
          "sum_product": LDPC_RULE_SUM_PRODUCT}
 (LDPC_KERNEL_AUTO, LDPC_KERNEL_ONCHIP_INT, LDPC_KERNEL_ONCHIP_HALF, LDPC_KERNEL_STREAM, LDPC_KERNEL_CLUSTER,
@@ -153,7 +154,7 @@ def ldpc_last_error() -> str:
 def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=3, norm_shift=2,
                 offset_f32=0.0, norm_f32=0.75, msg_sat=127, max_iter=20, early_stop=1,
                 norm=None, kernel="auto", schedule="flooding", **_ignored) -> ldpc_decode_params:
-    """Builds ldpc_decode_params from names ('int8'/'f32', 'ss_fixed'/'ss_1bit'/'two_scan',
+    """Builds ldpc_decode_params from names ('int8'/'f32', 'ss_fixed'/'ss_1bit'/'two_scan'/'two_scan_1bit',
     'plain'/'offset'/'normalized', 'flooding'/'layered').  ``norm`` is an alias for norm_f32."""
     if norm is not None:
         norm_f32 = norm
