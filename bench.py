@@ -8,8 +8,15 @@ whole job over all ranks; ``e2e`` is the same through the C ABI with the LLRs
 copied from pinned host memory and the decisions/iterations/flags copied back
 inside the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload qc_n7493]
-                  [--form ss_1bit|ss_fixed] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload irr_n64800]
+                  [--form ss_1bit|ss_fixed|two_scan|two_scan_1bit] [--impl ours|reference]
+
+The default workload is the largest single-GPU configuration: the N=64800 rate
+1/2 staircase code, 1024 frames, 50 iterations, int8, Section V form.  The same
+run times the comparison forms on the same frames (the per-edge single scan and
+the two-scan with per-edge or Section V message storage) and reports them under
+``comparisons``, with the single-scan/two-scan time ratios; it also measures the
+frame error rate at the workload's Eb/N0 with early stop on (``fer``).
 
 ``--workload multi8`` times the uneven eight-code batch (ldpc_multi_* plan,
 autotuned, one CUDA graph replay per step); ``--workload learned_qc_n7493`` one
@@ -265,7 +272,8 @@ def cpu_oracle_sample(w, form: str, budget_s: float, max_frames: int, layers=Non
         if layers is not None:
             oracle.decode_layered_int(w.code, q, layers, **kw)
         else:
-            oracle.decode_int(w.code, q, form=form, **kw)
+            # the two-scan with the Section V storage computes the two-scan's integers
+            oracle.decode_int(w.code, q, form="two_scan" if form == "two_scan_1bit" else form, **kw)
         t_total += time.perf_counter() - t0
         done += q.shape[0]
     gbps = done * w.K / t_total / 1e9
@@ -330,21 +338,28 @@ def run_reference(args, world, rank):
     w = I.make_workload(args.workload)
     w.params["early_stop"] = 0
     budget = float(os.environ.get("BENCH_REF_BUDGET_S", "4"))
-    per_step = []
+    per_step, step_ms = [], []
     info = None
     for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         info, sec_per_frame = cpu_oracle_sample(w, args.form, budget_s=budget if s >= args.warmup else 1.0,
                                                 max_frames=w.n_frames)
         if s >= args.warmup:
             per_step.append(info["value"])
+            step_ms.append((time.perf_counter() - t0) * 1e3)
     val = float(np.median(per_step))
     info["value"] = val
-    ms = w.n_frames * w.K / (val * 1e9) * 1e3
+    # each step decodes a bounded sample of the batch: ms_per_step is that
+    # sample's wall time, value its throughput; a whole-batch step would take
+    # full_batch_ms_estimate (the same throughput over all frames)
+    ms = float(np.median(step_ms))
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int8", "data": "synthetic",
             "config": {"workload": w.name, "form": args.form, "n_frames": w.n_frames,
-                       "iters": w.params["max_iter"], "N": w.code.n_vars, "K": w.K},
+                       "iters": w.params["max_iter"], "N": w.code.n_vars, "K": w.K,
+                       "step": "a bounded sample of the batch per step (cpu_baseline.sample)",
+                       "full_batch_ms_estimate": w.n_frames * w.K / (val * 1e9) * 1e3},
             "impl": "reference", "cpu_baseline": info,
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -635,12 +650,98 @@ def run_learned(args, world, rank, local):
     return 0
 
 
+COMPARE_FORMS = ("ss_1bit", "ss_fixed", "two_scan", "two_scan_1bit")
+
+
+def time_decode(ldpc, code, params, llr, F, flush, stream, dev, steps: int, warmup: int):
+    """Mean device ms of ldpc_decode_batch over `steps` decodes after `warmup`,
+    L2 flushed before each (outside the events)."""
+    import torch
+    ws_bytes = ldpc.ldpc_workspace_size(code.handle, params, F)
+    N8 = (code.n_vars + 7) // 8
+    bits = torch.empty((F, N8), dtype=torch.uint8, device=dev)
+    iters = torch.empty(F, dtype=torch.int32, device=dev)
+    ok = torch.empty(F, dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(ws_bytes, 1) + 256, dtype=torch.uint8, device=dev)
+    ws_ptr = (ws.data_ptr() + 255) & ~255
+
+    class _WS:
+        def data_ptr(self):
+            return ws_ptr
+
+    def one():
+        ldpc.ldpc_decode_batch(code.handle, params, llr, F, bits, iters, ok, None, _WS() if ws_bytes else None,
+                               ws_bytes, stream)
+
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            one()
+        for s in range(steps):
+            flush.fill_(s & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one()
+            b.record(stream)
+            evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in evs])), bits, iters, ok
+
+
+def compare_forms(ldpc, code, w, llr, F, main_form, flush, stream, dev, main_ms):
+    """The other forms on the same frames and iterations: per-edge single scan,
+    two-scan with per-edge messages, two-scan with the Section V state."""
+    peaks = measured_peaks()
+    out = {}
+    K, iters_cap = w.K, w.params["max_iter"]
+    for form in COMPARE_FORMS:
+        if form == main_form:
+            ms = main_ms
+            chosen = ldpc.ldpc_kernel_choice(code.handle, ldpc.make_params(form=form, **w.params), F)
+        else:
+            params = ldpc.make_params(form=form, **w.params)
+            try:
+                chosen = ldpc.ldpc_kernel_choice(code.handle, params, F)
+            except ldpc.LdpcError as e:
+                out[form] = {"unavailable": str(e)}
+                continue
+            ms, _, it, _ = time_decode(ldpc, code, params, llr, F, flush, stream, dev, steps=5, warmup=2)
+            assert int(it.min()) == iters_cap and int(it.max()) == iters_cap
+        ab = algorithmic_bytes(w.code, form, iters_cap, F)
+        out[form] = {"ms": ms, "value": F * K / (ms * 1e-3) / 1e9, "unit": UNIT, "kernel": chosen,
+                     "hbm_frac": ab["per_launch"] / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                     "bytes_per_frame_iter": ab["per_frame_iter"]}
+    ss = out.get("ss_1bit", {}).get("ms")
+    if ss:
+        out["two_scan_over_single_scan_time"] = {f: out[f]["ms"] / ss for f in ("two_scan", "two_scan_1bit")
+                                                 if "ms" in out.get(f, {})}
+    out["note"] = ("same frames, same fixed iteration count, early stop off, L2 flushed before each decode; "
+                   "hbm_frac = the form's streaming-model bytes over its time and the copy bandwidth")
+    return out
+
+
+def fer_point(ldpc, code, w, llr, F, form, stream, dev):
+    """Frame error rate of the benchmarked decoder at the workload's Eb/N0 with
+    early stop on: the decisions of every frame against its transmitted codeword
+    (random codewords of the code, BPSK over AWGN), Wilson 95 % interval."""
+    import torch
+    from paper_cs_0609090_gb300.fer import wilson
+    params = ldpc.make_params(form=form, **dict(w.params, early_stop=1))
+    _, bits, iters, ok = time_decode(ldpc, code, params, llr, F, torch.empty(1, device=dev), stream, dev, 1, 0)
+    dec = ldpc.unpack_bits(bits.cpu().numpy(), w.code.n_vars)
+    errors = int(np.any(dec != w.codewords, axis=1).sum())
+    return {"ebn0_db": w.ebn0_db, "frames": F, "errors": errors, "fer": errors / F, "wilson95": wilson(errors, F),
+            "mean_iters": float(iters.double().mean().item()), "max_iter": w.params["max_iter"],
+            "syndrome_ok": float(ok.double().mean().item()), "early_stop": 1,
+            "note": "one batch; the FER curves with >= 100 errors per point are in profiles/"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="qc_n7493")
+    ap.add_argument("--workload", default="irr_n64800")
     ap.add_argument("--form", default="ss_1bit", choices=["ss_1bit", "ss_fixed", "two_scan", "two_scan_1bit"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto",
@@ -649,6 +750,8 @@ def main():
     ap.add_argument("--schedule", default="flooding", choices=["flooding", "layered"],
                     help="layered: the single scan with column-disjoint layers updating in place")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparison forms and the FER measurement (profiling runs)")
     ap.add_argument("--frames", type=int, default=None,
                     help="decode this many frames of the workload instead of its batch (profiling runs)")
     ap.add_argument("--iters", type=int, default=None,
@@ -836,6 +939,9 @@ def main():
                                           else 3 + w.params["max_iter"] if kname == "pp2_rows"
                                           else 3 + 2 * w.params["max_iter"]),
             "roofline": roofline, "clocks": clocks}
+    if not args.no_compare and args.dtype == "int8" and args.schedule == "flooding" and world == 1:
+        line["comparisons"] = compare_forms(ldpc, code, w, llr, F, args.form, flush, stream, dev, ms_step)
+        line["fer"] = fer_point(ldpc, code, w, llr, F, args.form, stream, dev)
     if not args.no_cpu_baseline and args.dtype == "int8":
         lay = ldpc.ldpc_code_layers(code.handle, w.code.n_checks)[1] if args.schedule == "layered" else None
         info, _ = cpu_oracle_sample(w, args.form, budget_s=float(os.environ.get("BENCH_CPU_BUDGET_S", "12")),

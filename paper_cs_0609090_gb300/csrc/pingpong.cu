@@ -61,9 +61,11 @@ __device__ __forceinline__ uint32_t valid_bits(int p, int F) {
   return (2 * p < F ? 1u : 0u) | (2 * p + 1 < F ? 2u : 0u);
 }
 
-// 8-byte f16x2 atomic add of two frame pairs (no result).
+// 8-byte f16x2 atomic add of two frame pairs (no result).  No "memory" clobber:
+// within a row kernel only these atomics touch the buffer they add to, so the
+// compiler may move the next check's loads (other buffers) ahead of them.
 __device__ __forceinline__ void red_add_h2x2(uint32_t* p, uint32_t a, uint32_t b) {
-  asm volatile("red.global.add.noftz.v2.f16x2 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b) : "memory");
+  asm volatile("red.global.add.noftz.v2.f16x2 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b));
 }
 
 // L^(k)_j - L^(k-2)_j for successive positions j of one check and frame pair.
@@ -182,7 +184,9 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
 // degree-sorted order for the chunk's 64 pairs (warp w: checks bx kTile + w kRows
 // ..., lane l: pairs chunk 64 + 2 l, + 1).
 template <int FORM, bool ES>
-__global__ void __launch_bounds__(kWarps * 32, 3) pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
+// CTAs per SM (registers 65536 / (256 x this)), measured on the N=64800 code:
+// Section V 3 (8.68 ms; 4 spills and gives 8.77), per edge 4 (11.99 against 12.38)
+__global__ void __launch_bounds__(kWarps * 32, FORM == 1 ? 3 : 4) pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.y * 64 + 2 * lane;
   const int FP = s.FP;
@@ -325,18 +329,49 @@ __global__ void __launch_bounds__(kWarps * 32) pp2_final(const DevCode c, PP2 s,
   if (__all_sync(kFull, (aA | aB) == 0u)) return;
   const uint32_t* Zk = s.zb + (size_t)(K & 1) * c.N * FP + p;
   const int m0 = blockIdx.x * kTile + warp * kRows;
-  const int m1 = min(m0 + kRows, c.M);
+  const int nr = min(kRows, c.M - m0);
   uint32_t fa = 0, fb = 0;
-  for (int m = m0; m < m1; ++m) {
-    const int d = c.deg(m);
-    uint32_t ya = 0, yb = 0;
-    for (int j = 0; j < d; ++j) {
-      const uint2 v = *reinterpret_cast<const uint2*>(Zk + (size_t)c.col(j, m) * FP);
-      ya ^= dec_bits(v.x);
-      yb ^= dec_bits(v.y);
+  if (nr <= 0) return;
+  const int d0 = c.deg(m0);
+  if (nr == kRows && d0 == c.deg(m0 + nr - 1)) {
+    // every gather of the warp's checks goes out before the first is used; lane
+    // l < kRows d0 holds the handle of (check m0 + l / d0, position l % d0)
+    uint32_t hl = 0;
+    if (lane < kRows * d0) {
+      const int r = lane / d0, j = lane - r * d0;
+      hl = (uint32_t)c.col(j, m0 + r) * FP;
     }
-    fa |= ((ya >> 15) & 1u) | ((ya >> 30) & 2u);
-    fb |= ((yb >> 15) & 1u) | ((yb >> 30) & 2u);
+    uint2 v[kRows][8];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j < d0) v[r][j] = *reinterpret_cast<const uint2*>(Zk + __shfl_sync(kFull, hl, r * d0 + j));
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      uint32_t ya = 0, yb = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (j < d0) {
+          ya ^= dec_bits(v[r][j].x);
+          yb ^= dec_bits(v[r][j].y);
+        }
+      }
+      fa |= ((ya >> 15) & 1u) | ((ya >> 30) & 2u);
+      fb |= ((yb >> 15) & 1u) | ((yb >> 30) & 2u);
+    }
+  } else {
+    for (int m = m0; m < m0 + nr; ++m) {
+      const int d = c.deg(m);
+      uint32_t ya = 0, yb = 0;
+      for (int j = 0; j < d; ++j) {
+        const uint2 v = *reinterpret_cast<const uint2*>(Zk + (size_t)c.col(j, m) * FP);
+        ya ^= dec_bits(v.x);
+        yb ^= dec_bits(v.y);
+      }
+      fa |= ((ya >> 15) & 1u) | ((ya >> 30) & 2u);
+      fb |= ((yb >> 15) & 1u) | ((yb >> 30) & 2u);
+    }
   }
   fa &= aA;
   fb &= aB;
