@@ -326,8 +326,10 @@ LDPC_API ldpc_status ldpc_quantize_llr(const float *llr, int64_t n, float delta,
  *    or STREAM; otherwise LDPC_ERR_UNSUPPORTED.
  *  - A request whose scratch exceeds LDPC_NOALLOC_SCRATCH_BYTES is rejected with
  *    LDPC_ERR_UNSUPPORTED and a message giving both sizes; decode fewer frames
- *    per call.  (48 MiB holds 64 frames of an N = 64800, rate-1/2 code, or about
- *    780 frames of the N = 7493 code.)
+ *    per call.  (48 MiB holds 64 frames of an N = 64800, rate-1/2 code in either
+ *    form, and 768 frames of the N = 7493 code in the SS_1BIT form or 576 in the
+ *    SS_FIXED form; ldpc_workspace_size with kernel = LDPC_KERNEL_STREAM gives
+ *    the exact need of a request.)
  *  - The first call on a device looks up the array's device address (a CUDA
  *    runtime query, no allocation); make that first call before any stream
  *    capture on the device.
@@ -381,15 +383,21 @@ typedef struct {
  *                 16; default the smallest that fits every such code.
  *   queue         1 (default): dynamic work queue; 2: round-robin assignment.
  *   large         codes whose frame pair does not fit one CTA: 1 (default) the
- *                 streaming decoder after the persistent launch; 2 thread-block
- *                 clusters inside the persistent launch (the whole batch in one
- *                 kernel launch). */
+ *                 streaming decoder after the persistent launch (the ping-pong
+ *                 decoder for codes whose checks have degree <= 8, else the
+ *                 two-launch one); 2 thread-block clusters inside the
+ *                 persistent launch (the whole batch in one kernel launch).
+ *   overlap       the codes on the streaming decoder: 0 (default) in sequence on
+ *                 the caller's stream until ldpc_multi_autotune picks the faster
+ *                 schedule; 1 always in sequence; 2 always overlapped on side
+ *                 streams.  The autotuner keeps a schedule fixed by 1 or 2. */
 typedef struct {
   int32_t threads;
   int32_t team_threads;
   int32_t cluster;
   int32_t queue;
   int32_t large;
+  int32_t overlap;
 } ldpc_multi_tuning;
 
 typedef struct ldpc_multi ldpc_multi;

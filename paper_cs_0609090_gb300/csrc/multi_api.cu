@@ -25,7 +25,9 @@ struct ldpc_multi {
   std::vector<int32_t> is_cluster, pairs_per_cta;  // per job of `jobs` (is_cluster: 0, 1, 2 streaming)
   struct StreamJob {
     int job;                     // index into jobs
+    bool pingpong;               // the ping-pong decoder (checks of degree <= 8), else the two-launch one
     ldpc::StreamLayout layout;
+    ldpc::PingpongLayout pp;
     size_t offset;               // in the workspace
   };
   std::vector<StreamJob> streamed;
@@ -148,10 +150,19 @@ ldpc_status build(const std::vector<JobIn>& in, int form, const ldpc_multi_tunin
     const ldpc_decode_params& p = in[j].p;
     ldpc::MultiJob& m = jobs[j];
     if (cs_need[j] == 0) {
-      const ldpc::StreamLayout L =
-          ldpc::stream_layout(0, form, c->N, c->M, c->ell_w * c->M, in[j].F);
-      b.streamed.push_back({(int)j, L, b.ws_bytes});
-      b.ws_bytes += al256(L.total);
+      ldpc_multi::StreamJob sj{};
+      sj.job = (int)j;
+      sj.offset = b.ws_bytes;
+      sj.pingpong = ldpc::pingpong_int8_eligible(c->N, c->M, c->ell_w, c->max_row_deg, c->max_col_deg, p.msg_sat,
+                                                  form, in[j].F);
+      if (sj.pingpong) {
+        sj.pp = ldpc::pingpong_layout(form, c->N, c->M, c->ell_w, in[j].F);
+        b.ws_bytes += al256(sj.pp.total);
+      } else {
+        sj.layout = ldpc::stream_layout(0, form, c->N, c->M, c->ell_w * c->M, in[j].F);
+        b.ws_bytes += al256(sj.layout.total);
+      }
+      b.streamed.push_back(sj);
       b.is_cluster[j] = 2;
       b.es = b.es || p.early_stop != 0;
       continue;
@@ -278,13 +289,14 @@ ldpc_status build(const std::vector<JobIn>& in, int form, const ldpc_multi_tunin
 }
 
 ldpc_multi_tuning normalize(const ldpc_multi_tuning* t) {
-  ldpc_multi_tuning s = {1024, 128, 0, 1, 1};
+  ldpc_multi_tuning s = {1024, 128, 0, 1, 1, 0};
   if (t != nullptr) {
     if (t->threads) s.threads = t->threads;
     if (t->team_threads) s.team_threads = t->team_threads;
     if (t->cluster) s.cluster = t->cluster;
     if (t->queue) s.queue = t->queue;
     if (t->large) s.large = t->large;
+    s.overlap = t->overlap;
   }
   return s;
 }
@@ -298,6 +310,7 @@ ldpc_status check_tuning(const ldpc_multi_tuning& s) {
     return fail(LDPC_ERR_INVALID_ARG, "cluster %d is not 2, 4, 8 or 16", s.cluster);
   if (s.queue != 1 && s.queue != 2) return fail(LDPC_ERR_INVALID_ARG, "queue %d is not 1 or 2", s.queue);
   if (s.large != 1 && s.large != 2) return fail(LDPC_ERR_INVALID_ARG, "large %d is not 1 or 2", s.large);
+  if (s.overlap < 0 || s.overlap > 2) return fail(LDPC_ERR_INVALID_ARG, "overlap %d is not 0, 1 or 2", s.overlap);
   return LDPC_OK;
 }
 
@@ -315,6 +328,7 @@ ldpc_status replan(ldpc_multi* p, const ldpc_multi_tuning& s) {
   st = build(job_inputs(p->jobs), p->form, s, true, &b);
   if (st != LDPC_OK) return st;
   p->shape = s;
+  if (s.overlap != 0) p->overlap = s.overlap == 2;  // 1 / 2 fix the schedule; 0 keeps the current one
   p->mp = b.mp;
   p->threads = b.threads;
   p->grid = b.grid;
@@ -393,9 +407,14 @@ cudaError_t launch_plan(const ldpc_multi* p, void* ws, cudaStream_t st) {
     r.num = jb.params.norm_num;
     r.shift = jb.params.norm_shift;
     r.qm = jb.params.msg_sat;
-    e = ldpc::stream_int8_decode(view(jb.code), r, p->form, sj.layout, static_cast<char*>(ws) + sj.offset,
-                                 jb.code->sm_count, jb.llr, jb.n_frames, jb.params.max_iter, jb.params.early_stop,
-                                 jb.hard_bits, jb.iters_used, jb.syndrome_ok, jb.llr_out, ss);
+    if (sj.pingpong)
+      e = ldpc::pingpong_int8_decode(view(jb.code), r, p->form, sj.pp, static_cast<char*>(ws) + sj.offset, jb.llr,
+                                     jb.n_frames, jb.params.max_iter, jb.params.early_stop, jb.hard_bits,
+                                     jb.iters_used, jb.syndrome_ok, jb.llr_out, ss);
+    else
+      e = ldpc::stream_int8_decode(view(jb.code), r, p->form, sj.layout, static_cast<char*>(ws) + sj.offset,
+                                   jb.code->sm_count, jb.llr, jb.n_frames, jb.params.max_iter, jb.params.early_stop,
+                                   jb.hard_bits, jb.iters_used, jb.syndrome_ok, jb.llr_out, ss);
     if (e != cudaSuccess) return e;
     if (fork) {
       e = cudaEventRecord(p->joined[i], ss);
@@ -617,7 +636,10 @@ ldpc_status ldpc_multi_autotune(ldpc_multi* plan, void* workspace, size_t ws_byt
     s = replan(plan, best);
     // the chosen shape with and without the streamed codes overlapped, timed
     // back to back over at least 5 launches each; the faster is kept
-    if (s == LDPC_OK && !plan->streamed.empty()) {
+    if (s == LDPC_OK && !plan->streamed.empty() && start.overlap != 0) {
+      plan->shape.overlap = start.overlap;  // fixed by the caller: kept
+      plan->overlap = start.overlap == 2;
+    } else if (s == LDPC_OK && !plan->streamed.empty()) {
       const int n = reps > 5 ? reps : 5;
       float t_seq = 0.0f, t_ovl = 0.0f;
       plan->overlap = false;

@@ -34,6 +34,10 @@ class LearnedDecoder:
         self.ws_bytes = ldpc.ldpc_learned_workspace_size(code.handle, self.K, self.max_frames)
         self._ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
         self.frames = 0  # frames of the last forward
+        # Number of forwards run so far: the workspace holds the checkpoints of
+        # the latest one only, and a backward through an earlier one must not
+        # read them.
+        self.generation = 0
 
     def ws(self):
         base = (self._ws.data_ptr() + 255) & ~255
@@ -52,6 +56,7 @@ class LearnedDecoder:
         z = torch.empty((F, N), dtype=torch.float32, device=llr.device) if want_z else None
         ldpc.ldpc_learned_forward(self.code.handle, self.K, beta, llr, F, z, self.ws(), self.ws_size(F))
         self.frames = F
+        self.generation += 1
         return z
 
     def loss(self, target_bits=None, want_grad: bool = True) -> torch.Tensor:
@@ -69,7 +74,13 @@ class LearnedDecoder:
 
 class LearnedOffsetDecode(torch.autograd.Function):
     """Z^(K) = decode(llr; beta) with the hand-written adjoint as its backward.
-    Gradients flow to ``beta`` only (the channel values are data)."""
+    Gradients flow to ``beta`` only (the channel values are data).
+
+    The adjoint reads the per-iteration checkpoints that the forward left in the
+    decoder's workspace, and a decoder keeps those of its latest forward only.
+    So the backward of an apply must run before the next apply on the same
+    decoder (or use one decoder per apply); otherwise it raises instead of
+    returning the gradient of the wrong frames."""
 
     @staticmethod
     def forward(ctx, llr, beta, decoder: LearnedDecoder):
@@ -77,12 +88,18 @@ class LearnedOffsetDecode(torch.autograd.Function):
         beta_c = beta.detach().contiguous().float()
         z = decoder.forward(llr, beta_c)
         ctx.decoder = decoder
+        ctx.generation = decoder.generation
         ctx.save_for_backward(beta_c)
         return z
 
     @staticmethod
     def backward(ctx, grad_z):
         (beta_c,) = ctx.saved_tensors
+        if ctx.decoder.generation != ctx.generation:
+            raise RuntimeError(
+                f"LearnedOffsetDecode.backward: the decoder ran {ctx.decoder.generation - ctx.generation} "
+                "forward(s) after this one, so its workspace no longer holds this forward's checkpoints; "
+                "run backward before the next apply or use a separate LearnedDecoder per apply")
         db = ctx.decoder.backward(beta_c, grad_z.contiguous().float())
         return None, db, None
 

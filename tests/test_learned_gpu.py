@@ -153,6 +153,34 @@ def test_autograd_function(env):
     assert torch.allclose(beta.grad, direct, rtol=1e-4, atol=1e-9)
 
 
+def test_autograd_two_applies_then_backward_raises(env):
+    """A decoder keeps the checkpoints of its latest forward only: the backward of
+    an earlier apply must refuse to run on them, and one decoder per apply gives
+    both gradients right."""
+    torch, learned = env["torch"], env["learned"]
+    code, h = env["code"], env["h"]
+    w = I.make_workload("qc_n7493", n_frames=4, ebn0_db=2.5, zero_codeword=True)
+    llr1 = torch.from_numpy(w.llr.astype(np.float32)).cuda()
+    llr2 = torch.from_numpy((w.llr[::-1] * 0.9).astype(np.float32).copy()).cuda()
+    dec = learned.LearnedDecoder(h, 3, 4)
+    beta = torch.full((3, dec.C), 0.3, dtype=torch.float32, device="cuda", requires_grad=True)
+    z1 = learned.LearnedOffsetDecode.apply(llr1, beta, dec)
+    z2 = learned.LearnedOffsetDecode.apply(llr2, beta, dec)
+    with pytest.raises(RuntimeError, match="no longer holds"):
+        torch.autograd.grad(z1.sum(), beta, retain_graph=True)
+    (g2,) = torch.autograd.grad(z2.sum(), beta)  # the latest apply is fine
+    # two decoders: each backward matches its own single-apply gradient
+    d1, d2 = learned.LearnedDecoder(h, 3, 4), learned.LearnedDecoder(h, 3, 4)
+    a1 = learned.LearnedOffsetDecode.apply(llr1, beta, d1)
+    a2 = learned.LearnedOffsetDecode.apply(llr2, beta, d2)
+    (ga1,) = torch.autograd.grad(a1.sum(), beta)
+    (ga2,) = torch.autograd.grad(a2.sum(), beta)
+    solo = learned.LearnedDecoder(h, 3, 4)
+    (gs1,) = torch.autograd.grad(learned.LearnedOffsetDecode.apply(llr1, beta, solo).sum(), beta)
+    # (float atomics in the forward: equal up to rounding)
+    assert torch.allclose(ga1, gs1, rtol=1e-4, atol=1e-6) and torch.allclose(ga2, g2, rtol=1e-4, atol=1e-6)
+
+
 def test_adam_step(env):
     torch, ldpc = env["torch"], env["ldpc"]
     rng = np.random.default_rng(0)

@@ -134,13 +134,19 @@ def test_multi_batch_local_only_and_subteams(L, form):
         _multi_check(L, mb, ws, _multi_oracle(ws, form))
 
 
-def test_multi_batch_cuda_graph_replay(L):
+@pytest.mark.parametrize("overlap", [1, 2])
+def test_multi_batch_cuda_graph_replay(L, overlap):
     """The launch is captured once in a CUDA graph and replayed on new channel
-    values written into the same input buffers."""
+    values written into the same input buffers; the three codes on the
+    streaming decoder in sequence (overlap 1) or forked onto side streams and
+    joined back (overlap 2), checked directly and after the replays."""
     import torch
     form = "ss_1bit"
     ws = I.make_multi_workload(frames=[5, 4, 3, 6, 5, 2, 2, 1], frame_seed=7)
-    mb, codes, llrs = _batch(L, ws, form)
+    mb, codes, llrs = _batch(L, ws, form, L.ldpc_multi_tuning(0, 0, 0, 0, 0, overlap))
+    assert mb.info()["overlap"] == overlap
+    mb.decode()
+    _multi_check(L, mb, ws, _multi_oracle(ws, form))
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
@@ -159,13 +165,18 @@ def test_multi_batch_cuda_graph_replay(L):
         _multi_check(L, mb, ws2, _multi_oracle(ws2, form))
 
 
-def test_multi_batch_autotune(L):
+@pytest.mark.parametrize("overlap", [0, 2])
+def test_multi_batch_autotune(L, overlap):
+    """The autotuner picks a shape (and, with overlap 0, the schedule of the
+    streamed codes); a schedule fixed by the caller (2) is kept."""
     form = "ss_fixed"
     ws = I.make_multi_workload(frames=[8, 6, 4, 5, 7, 3, 2, 2], frame_seed=11)
-    mb, _, _ = _batch(L, ws, form, want_llr=False)
+    mb, _, _ = _batch(L, ws, form, L.ldpc_multi_tuning(0, 0, 0, 0, 0, overlap), want_llr=False)
     shape, ms = mb.autotune(reps=1)
     assert ms > 0 and shape.threads in (512, 1024) and shape.team_threads in (64, 128, 256)
     assert shape.large in (1, 2)
+    if overlap:
+        assert shape.overlap == overlap and mb.info()["overlap"] == overlap
     for bits, iters, ok, _ in mb.outputs:
         bits.zero_(), iters.fill_(-1), ok.fill_(7)
     mb.decode()
