@@ -57,8 +57,14 @@ def _forward(env, q, beta_kc, K):
     return dec, beta, z
 
 
-def test_learned_forward_matches_fp64(env):
-    w = I.make_workload("qc_n7493", n_frames=16, ebn0_db=2.0, zero_codeword=True)
+@pytest.mark.parametrize("ebn0", [2.0, 3.0])
+def test_learned_forward_matches_fp64(env, ebn0):
+    """Posteriors after 10 iterations against the FP64 oracle with the same
+    per-iteration offsets.  Frames that decode are held to 1e-5 relative; at
+    2.0 dB none does, and the offset rule amplifies float32 rounding on those
+    oscillating trajectories (measured on this code: 8e-6 after 5 iterations,
+    5e-4 after 12), so frames away from the decision threshold take 5e-4."""
+    w = I.make_workload("qc_n7493", n_frames=16, ebn0_db=ebn0, zero_codeword=True)
     K = 10
     beta_kc = np.random.default_rng(2).uniform(0.1, 0.6, size=(K, 2))
     q = w.llr.astype(np.float32).astype(np.float64)
@@ -69,6 +75,11 @@ def test_learned_forward_matches_fp64(env):
     clean = o.margin > 1e-4
     err = np.abs(g - o.z) / np.maximum(1.0, np.abs(o.z))
     assert err[clean].max() <= 5e-4, err[clean].max()
+    dec = clean & (o.ok == 1)
+    if ebn0 >= 3.0:
+        assert dec.sum() >= 12, dec.sum()
+    if dec.any():
+        assert err[dec].max() <= 1e-5, err[dec].max()
 
 
 def _ref_class_grad(code, q, tab):

@@ -44,22 +44,24 @@ def test_tree_codes_reach_app_llr(L, seed):
 
 
 def test_matches_fp64_oracle(L):
-    """Frames whose FP64 trajectory stays 1e-3 away from the decision threshold
-    (sum-product posteriors pass near zero more often than min-sum's: 164 of
-    300 frames at 1.8 dB kept that margin): iterations, flags and decisions
-    equal, posteriors of decoded frames within 1e-3 relative."""
-    w = I.make_workload("reg36_n1008", n_frames=300, ebn0_db=2.5)
+    """Frames whose FP64 trajectory keeps 1e-4 away from the decision threshold
+    (295 of 300 at 3.0 dB): iterations, flags and decisions equal, posteriors of
+    decoded frames within 1e-5 relative.  Measured without early stop on this
+    code at 3.0 dB, the float32 posteriors of those frames stay within 4.5e-6 of
+    FP64 at every iteration count up to 30."""
+    w = I.make_workload("reg36_n1008", n_frames=300, ebn0_db=3.0)
     llr = w.llr.astype(np.float32)
     g = _spa(L, w.code, llr, 30, early_stop=1)
     o = oracle.decode_f64(w.code, llr.astype(np.float64), form="ss_fixed", rule="sum_product", max_iter=30,
                           early_stop=1, want_margin=True)
-    clean = o.margin >= 1e-3
-    assert clean.sum() >= 0.5 * clean.size
+    clean = o.margin >= 1e-4
+    assert clean.sum() >= 0.9 * clean.size, (~clean).sum()
     for key in ("iters", "ok", "bits"):
         assert np.array_equal(g[key][clean], o[key][clean]), key
     conv = clean & (o.ok == 1)
+    assert conv.sum() >= 0.9 * clean.size
     err = np.abs(g["z"][conv] - o.z[conv]) / np.maximum(1.0, np.abs(o.z[conv]))
-    assert err.max() <= 1e-3, err.max()
+    assert err.max() <= 1e-5, err.max()
 
 
 def test_fewer_frame_errors_than_min_sum(L):
@@ -87,18 +89,25 @@ def test_rejected_outside_the_float_per_edge_path(L):
 
 def test_fer_tool_counts_errors_against_the_decoder_outputs(L):
     """paper_cs_0609090_gb300.fer on a few frames: its error count equals the
-    count taken directly from the same decoder on the same device frames."""
+    count taken directly from the same decoder on the same device frames (random
+    codewords of the code, each frame with its own noise)."""
     import torch
     from paper_cs_0609090_gb300 import fer as fer_mod
     w = I.make_workload("reg36_n1008", n_frames=1, with_llr=False)
     code = L.Code.from_inputs(w.code)
     rate = (w.code.n_vars - w.code.n_checks) / w.code.n_vars
     params = L.make_params(**w.params)
-    r = fer_mod.fer(code, params, 300, 1.5, rate=rate, delta=w.delta, qc=w.qc, seed=5, batch=128)
+    pool = fer_mod.CodewordPool(w.code, 50, seed=3, device=torch.device("cuda"))
+    run = fer_mod.int8_decoder(code, params, w.delta, w.qc, 128, torch.device("cuda"))
+    r = fer_mod.run_point(run, w.code.n_vars, rate, 1.5, pool, min_errors=10 ** 9, max_frames=300, batch=128, seed=5)
+    packed, cw = pool.rows(0, 300, torch.device("cuda"))
     llr = torch.empty((300, w.code.n_vars), dtype=torch.float32, device="cuda")
-    L.ldpc_awgn_llr_f32(w.code.n_vars, 5, 0, 300, 1.5, 1.5, rate, None, llr)
+    L.ldpc_awgn_llr_f32(w.code.n_vars, 5, 0, 300, 1.5, 1.5, rate, packed, llr)
     q = torch.empty((300, w.code.n_vars), dtype=torch.int8, device="cuda")
     L.ldpc_quantize_llr(llr, 300 * w.code.n_vars, w.delta, w.qc, q)
     bits, iters, _, _ = L.decode(code, q, params)
-    assert r["frames"] == 300 and r["errors"] == int((bits != 0).any(dim=1).sum().item())
+    dec = L.unpack_bits(bits.cpu().numpy(), w.code.n_vars)
+    assert r["frames"] == 300 and r["errors"] == int(np.any(dec != cw.cpu().numpy(), axis=1).sum())
     assert abs(r["mean_iters"] - float(iters.double().mean().item())) < 1e-9
+    # every transmitted word is a codeword
+    assert np.all(I.syndrome(w.code, cw.cpu().numpy()) == 0)
