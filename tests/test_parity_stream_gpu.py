@@ -16,14 +16,16 @@ pytestmark = pytest.mark.gpu
 # |Z_gpu - Z_fp64| <= RTOL * max(1, |Z_fp64|).  The normalized rule (lambda < 1)
 # scales every rounding error down at each check, so RTOL holds for every frame
 # after 30 iterations (measured 8.7e-6 on the N=1008 code at 2.0 dB).  The offset
-# rule has no such contraction: on frames that decode, the error stays at the
-# rounding level (<= 3.4e-6 after 30 iterations, N=1008), but on frames that never
-# reach a codeword the oscillating trajectory amplifies it about tenfold every four
+# rule has no such contraction: while a frame has not reached a codeword its
+# oscillating trajectory amplifies the rounding error about tenfold every four
 # iterations (N=7493 at 2.5 dB, offset 0.5: 6e-7 after 1, 8e-6 after 5, 5e-4 after
-# 12, 9e-2 after 20).  Decoded frames are held to RTOL under either rule; the
-# all-frames offset check runs 12 iterations at 3.3 dB and takes RTOL_OFFSET.
+# 12, 9e-2 after 20; N=1008 at 2.0 dB: 6.1e-6 after 12, 5e-5 after 20), and a frame
+# that decodes late keeps what it gathered (1.2e-4 measured).  Offset frames that
+# stop within OFFSET_TIGHT_ITERS iterations are held to RTOL, later ones and the
+# 12-iteration all-frames check to RTOL_OFFSET.
 RTOL = 1e-5
 RTOL_OFFSET = 5e-4
+OFFSET_TIGHT_ITERS = 10
 
 
 @pytest.fixture(scope="module")
@@ -142,9 +144,9 @@ MARGIN = 1e-4
 def test_f32_early_stop_regular(L, form, rule, offset):
     """Frames away from the decision boundary: iteration counts, flags and
     decisions equal the FP64 oracle's.  Frames the oracle decodes to a codeword
-    have posteriors within RTOL under both rules; frames that run to the cap
-    without one are excluded from that check (under the offset rule rounding
-    grows along their oscillating trajectory)."""
+    have posteriors within RTOL (under the offset rule: those that stop within
+    OFFSET_TIGHT_ITERS iterations; later ones within RTOL_OFFSET); frames that
+    run to the cap without one are excluded from that check."""
     w = I.make_workload("reg36_n1008", n_frames=400, ebn0_db=2.0)
     g, o = _f32(L, w.code, w.llr, form, rule, offset=offset, max_iter=30, early_stop=1)
     clean = o.margin >= MARGIN
@@ -154,8 +156,11 @@ def test_f32_early_stop_regular(L, form, rule, offset):
     assert np.array_equal(g["bits"][clean], o.bits[clean])
     conv = clean & (o.ok == 1)
     assert conv.sum() >= 0.8 * clean.size
-    err = np.abs(g["z"][conv] - o.z[conv]) / np.maximum(1.0, np.abs(o.z[conv]))
-    assert err.max() <= RTOL, f"max relative error {err.max():.3g}"
+    err = np.abs(g["z"] - o.z) / np.maximum(1.0, np.abs(o.z))
+    tight = conv & (o.iters <= OFFSET_TIGHT_ITERS) if rule == "offset" else conv
+    assert tight.sum() >= 0.5 * clean.size
+    assert err[tight].max() <= RTOL, f"max relative error {err[tight].max():.3g}"
+    assert err[conv].max() <= RTOL_OFFSET, f"max relative error {err[conv].max():.3g}"
 
 
 def _clean_parity(g, o, rtol, min_clean=0.9):
@@ -209,8 +214,6 @@ def test_f32_other_degrees(L, form):
     g, o = _f32(L, w.code, w.llr[:40], form, "offset", offset=0.25, max_iter=12, early_stop=0)
     err = np.abs(g["z"] - o.z) / np.maximum(1.0, np.abs(o.z))
     assert err.max() <= RTOL_OFFSET, f"max relative error {err.max():.3g}"
-    dec = (o.ok == 1) & (o.margin >= MARGIN)
-    assert dec.sum() >= 20 and err[dec].max() <= RTOL, (dec.sum(), err[dec].max())
 
 
 def test_stream_workspace_contract(L):
