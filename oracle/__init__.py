@@ -48,7 +48,7 @@ class _IParams(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_int32), ("offset", ctypes.c_int32),
                 ("norm_num", ctypes.c_int32), ("norm_shift", ctypes.c_int32),
                 ("msg_sat", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("early_stop", ctypes.c_int32)]
+                ("early_stop", ctypes.c_int32), ("post_sat", ctypes.c_int32)]
 
 
 class _DParams(ctypes.Structure):
@@ -101,10 +101,12 @@ def _code_struct(row_ptr, col_idx, n_vars):
 
 
 def decode_int(code, q0, *, form="ss_1bit", rule="plain", offset=0, norm_num=3, norm_shift=2,
-               msg_sat=127, max_iter=20, early_stop=1, want_l=False, want_state=False,
+               msg_sat=127, max_iter=20, early_stop=1, post_sat=0, want_l=False, want_state=False,
                threads=0) -> Result:
     """Integer min-sum decode of q0 (int [F, N]) with the given form and rule.
-    ``code`` is any object with n_vars, row_ptr, col_idx."""
+    ``code`` is any object with n_vars, row_ptr, col_idx.  ``post_sat`` > 0
+    stores the posterior saturated to [-post_sat, post_sat] after every
+    iteration (single-scan forms; 127: an int8 posterior)."""
     lib = _load()
     q = np.ascontiguousarray(np.atleast_2d(q0), dtype=np.int32)
     F, N = q.shape
@@ -113,7 +115,7 @@ def decode_int(code, q0, *, form="ss_1bit", rule="plain", offset=0, norm_num=3, 
     E = int(keep[0][-1])
     M = keep[0].size - 1
     p = _IParams(RULES[rule], int(offset), int(norm_num), int(norm_shift), int(msg_sat),
-                 int(max_iter), int(early_stop))
+                 int(max_iter), int(early_stop), int(post_sat))
     bits = np.zeros((F, N), np.uint8)
     iters = np.zeros(F, np.int32)
     ok = np.zeros(F, np.uint8)
@@ -151,7 +153,7 @@ def decode_layered_int(code, q0, layer, *, rule="plain", offset=0, norm_num=3, n
     E = int(keep[0][-1])
     lay = np.ascontiguousarray(layer, dtype=np.int32)
     p = _IParams(RULES[rule], int(offset), int(norm_num), int(norm_shift), int(msg_sat),
-                 int(max_iter), int(early_stop))
+                 int(max_iter), int(early_stop), 0)
     bits = np.zeros((F, N), np.uint8)
     iters = np.zeros(F, np.int32)
     ok = np.zeros(F, np.uint8)

@@ -42,6 +42,13 @@ static int64_t sat_i(const orc_iparams *p, int64_t mag) {
   return (p->msg_sat > 0 && mag > p->msg_sat) ? p->msg_sat : mag;
 }
 
+/* The stored posterior of the single scan: Z clamped to [-post_sat, post_sat]
+   when the posterior is kept in b bits, else Z itself. */
+static void sat_post(const orc_iparams *p, int64_t *Z, int32_t N) {
+  if (p->post_sat <= 0) return;
+  for (int32_t n = 0; n < N; ++n) Z[n] = Z[n] > p->post_sat ? p->post_sat : (Z[n] < -p->post_sat ? -p->post_sat : Z[n]);
+}
+
 /* Decoding step (Section III): x_n = 0 if Z_n > 0, else 1.  Returns 1 when
    H x^T = 0. */
 static int decide_and_check(const orc_code *c, const int64_t *Zi, const double *Zd,
@@ -228,6 +235,7 @@ static void decode_frame_int(const orc_code *c, const orc_csc *t, const orc_ipar
           }
         }
       }
+      if (form != ORC_TWO_SCAN) sat_post(p, Z, N);
       sat = decide_and_check(c, Z, NULL, w->x);
       if (p->early_stop && sat) break;
     }
@@ -532,6 +540,7 @@ int orc_decode_int(const orc_code *code, const orc_iparams *p, int32_t form, con
                    int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok, int32_t *z_out,
                    int32_t *l_out, int32_t *state_out, int32_t n_threads) {
   if (validate(code, form) || !p || p->max_iter < 0 || n_frames < 0) return -1;
+  if (form == ORC_TWO_SCAN && p->post_sat > 0) return -1; /* Z_mn, not a stored Z_n */
   if (n_frames == 0) return 0;
   if (!q0 || !bits || !iters || !ok || !z_out) return -1;
   job proto;
@@ -546,6 +555,7 @@ int orc_decode_layered_int(const orc_code *code, const orc_iparams *p, const int
                            const int32_t *q0, int32_t n_frames, uint8_t *bits, int32_t *iters, uint8_t *ok,
                            int32_t *z_out, int32_t *l_out, int32_t n_threads) {
   if (validate(code, ORC_SS_FIXED) || !p || p->max_iter < 0 || n_frames < 0 || !layer || n_layers < 1) return -1;
+  if (p->post_sat > 0) return -1; /* the layered update keeps Z exact */
   /* every check in a layer; the checks of a layer share no variable */
   int32_t *owner = (int32_t *)malloc(sizeof(int32_t) * ((size_t)code->n_vars * (size_t)n_layers + 1));
   if (!owner) return -1;

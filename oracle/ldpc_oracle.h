@@ -58,6 +58,11 @@ typedef struct {
   int32_t msg_sat;    /* Qm: |input| saturates to Qm before the min; <= 0: none */
   int32_t max_iter;
   int32_t early_stop; /* 1: stop at the first iteration whose decisions satisfy H */
+  /* > 0: the posterior is stored in b bits, Z^(k)_n = sat(Z^(0)_n + sum_m L^(k)_mn)
+     clamped to [-post_sat, post_sat] after every iteration (the b-bit storage of
+     Section IV's cost argument applied to Z; single-scan forms only, since the
+     two-scan form keeps Z_mn, not Z_n); <= 0: Z held exactly. */
+  int32_t post_sat;
 } orc_iparams;
 
 typedef struct {
