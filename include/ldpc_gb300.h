@@ -137,6 +137,19 @@ enum { LDPC_RULE_PLAIN = 0, LDPC_RULE_OFFSET = 1, LDPC_RULE_NORMALIZED = 2, LDPC
  *              rule is checked after whole iterations.  int8, SS_FIXED or
  *              SS_1BIT, kernel AUTO, the binary16 conditions of ONCHIP_HALF
  *              (N unrestricted); needs a workspace.
+ *   posterior  LDPC_POSTERIOR_EXACT (0): the int8 path holds every posterior
+ *              exactly (it fits int16; the two-scan, single-scan and Section V
+ *              forms then give identical results, Section V's equivalence).
+ *              LDPC_POSTERIOR_SAT8 (1): the posterior is stored in 8 bits, the
+ *              b-bit storage Section IV counts for messages applied to Z_n:
+ *              after every iteration Z^(k)_n = clamp(Z^(0)_n + sum_m L^(k)_mn,
+ *              -127, 127), and the next iteration's inputs Z^(k)_n - L^(k)_mn
+ *              read the clamped value; llr_out returns the clamped posteriors.
+ *              A single-scan-only variant (the two-scan form keeps Z_mn, not
+ *              Z_n) and no longer equivalent to two-scan: int8, SS_FIXED or
+ *              SS_1BIT, flooding, kernel AUTO, ONCHIP_HALF or STREAM (the
+ *              kernels that write the posterior in a column pass); otherwise
+ *              LDPC_ERR_UNSUPPORTED.  The float path takes EXACT only.
  */
 typedef struct {
   int32_t dtype;
@@ -152,9 +165,11 @@ typedef struct {
   int32_t early_stop;
   int32_t kernel;
   int32_t schedule;
+  int32_t posterior;
 } ldpc_decode_params;
 
 enum { LDPC_SCHEDULE_FLOODING = 0, LDPC_SCHEDULE_LAYERED = 1 };
+enum { LDPC_POSTERIOR_EXACT = 0, LDPC_POSTERIOR_SAT8 = 1 };
 
 enum {
   LDPC_KERNEL_AUTO = 0,
@@ -178,6 +193,37 @@ enum {
  * until ldpc_code_destroy.  Synchronous. */
 LDPC_API ldpc_status ldpc_code_create(ldpc_code **out, int32_t n_vars, int32_t n_checks,
                              const int32_t *row_ptr, const int32_t *col_idx, int device);
+
+/* A quasi-cyclic parity-check matrix (the structure of the DTMB codes the paper
+ * decodes, Section I): an mb x nb base matrix of circulant shifts lifted by z.
+ * Entry (i, j) = s in [0, z) puts the z x z identity shifted cyclically by s
+ * in block (i, j): check i z + r has variable j z + ((r + s) mod z); s = -1 is
+ * the zero block.  The caller owns `shift`. */
+typedef struct {
+  int32_t base_rows;      /* mb >= 1 */
+  int32_t base_cols;      /* nb >= 1 */
+  int32_t lift;           /* z >= 1 */
+  const int32_t *shift;   /* host, [mb][nb] row-major, each -1 or in [0, z) */
+} ldpc_qc_desc;
+
+/* Expands a QC descriptor into the check->variable adjacency ldpc_code_create
+ * takes (host computation only, no device call).
+ *   row_ptr   host or NULL, [mb z + 1].
+ *   col_idx   host or NULL, capacity entries; the variables of a check come in
+ *             increasing order (block column order).
+ *   n_edges   host or NULL: the number of edges E (call with col_idx NULL
+ *             and capacity 0 to size col_idx).
+ * LDPC_ERR_INVALID_ARG for a malformed descriptor (sizes < 1, a shift outside
+ * {-1} u [0, z), nb z, mb z or E beyond int32) or capacity < E with col_idx
+ * given. */
+LDPC_API ldpc_status ldpc_qc_expand(const ldpc_qc_desc *qc, int32_t *row_ptr, int32_t *col_idx,
+                                    int64_t capacity, int32_t *n_edges);
+
+/* ldpc_code_create of the expanded descriptor (n_vars = nb z, n_checks = mb z),
+ * with the block rows as the layers of the layered schedule (the z checks of a
+ * block row share no variable, since every block is a permutation).  Same
+ * checks and ownership as ldpc_code_create. */
+LDPC_API ldpc_status ldpc_code_create_qc(ldpc_code **out, const ldpc_qc_desc *qc, int device);
 
 /* Release a code (NULL is accepted).  Synchronises the code's device first. */
 LDPC_API ldpc_status ldpc_code_destroy(ldpc_code *code);

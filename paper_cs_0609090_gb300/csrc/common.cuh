@@ -52,6 +52,7 @@ struct IntRule {
   int32_t num;
   int32_t shift;
   int32_t qm;     // message saturation Qm
+  int32_t psat;   // > 0: the stored posterior is clamped to [-psat, psat] (8-bit posterior); 0: exact
   __device__ __forceinline__ int32_t g(int32_t mag) const {
     if (rule == 1) return max(mag - beta, 0);
     if (rule == 2) return (mag * num) >> shift;

@@ -130,6 +130,14 @@ ldpc_status check_params(const ldpc_code* c, const ldpc_decode_params* p) {
     return fail(LDPC_ERR_INVALID_ARG, "kernel %d is not a known LDPC_KERNEL_*", p->kernel);
   if (p->schedule != LDPC_SCHEDULE_FLOODING && p->schedule != LDPC_SCHEDULE_LAYERED)
     return fail(LDPC_ERR_INVALID_ARG, "schedule %d is not a known LDPC_SCHEDULE_*", p->schedule);
+  if (p->posterior != LDPC_POSTERIOR_EXACT && p->posterior != LDPC_POSTERIOR_SAT8)
+    return fail(LDPC_ERR_INVALID_ARG, "posterior %d is not a known LDPC_POSTERIOR_*", p->posterior);
+  if (p->posterior == LDPC_POSTERIOR_SAT8 &&
+      (p->dtype != LDPC_DTYPE_INT8 || (p->form != LDPC_FORM_SS_FIXED && p->form != LDPC_FORM_SS_1BIT) ||
+       p->schedule != LDPC_SCHEDULE_FLOODING ||
+       (p->kernel != LDPC_KERNEL_AUTO && p->kernel != LDPC_KERNEL_ONCHIP_HALF && p->kernel != LDPC_KERNEL_STREAM)))
+    return fail(LDPC_ERR_UNSUPPORTED, "the 8-bit posterior runs int8 single-scan decodes (SS_FIXED or SS_1BIT), "
+                "flooding, on kernel AUTO, ONCHIP_HALF or STREAM");
   if (p->dtype == LDPC_DTYPE_INT8) {
     if (p->msg_sat < 1 || p->msg_sat > 127)
       return fail(LDPC_ERR_INVALID_ARG, "msg_sat %d outside [1, 127]", p->msg_sat);
@@ -196,12 +204,15 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
   }
   if (p->dtype == LDPC_DTYPE_INT8 && (p->form == LDPC_FORM_SS_1BIT || p->form == LDPC_FORM_SS_FIXED)) {
     const int form = p->form == LDPC_FORM_SS_1BIT ? 1 : 0;
+    // the 8-bit posterior is clamped where a column pass writes it: the packed
+    // frame-resident kernel and the two-launch streaming kernel
+    const bool exact = p->posterior == LDPC_POSTERIOR_EXACT;
     const bool want_half = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_HALF;
-    const bool want_int = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_INT;
+    const bool want_int = exact && (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_ONCHIP_INT);
     const bool want_stream = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_STREAM;
-    const bool want_cluster = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_CLUSTER;
-    const bool want_persist = p->kernel == LDPC_KERNEL_PERSISTENT;
-    const bool want_pingpong = p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_PINGPONG;
+    const bool want_cluster = exact && (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_CLUSTER);
+    const bool want_persist = exact && p->kernel == LDPC_KERNEL_PERSISTENT;
+    const bool want_pingpong = exact && (p->kernel == LDPC_KERNEL_AUTO || p->kernel == LDPC_KERNEL_PINGPONG);
     if (want_half && ldpc::onchip_h2_eligible(c->N, c->max_row_deg, c->max_col_deg, p->msg_sat, p->rule, p->norm_num) &&
         ldpc::onchip_h2_plan(v, form, n_frames, c->sm_count, c->smem_optin, c->max_row_deg, &ch->onchip)) {
       ch->kind = Choice::ONCHIP_H2;
@@ -565,6 +576,7 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
   r.num = params->norm_num;
   r.shift = params->norm_shift;
   r.qm = params->msg_sat;
+  r.psat = params->posterior == LDPC_POSTERIOR_SAT8 ? 127 : 0;
   const int form = params->form == LDPC_FORM_SS_1BIT ? 1 : 0;
   if (ch.kind == Choice::ONCHIP_TWOSCAN) {
     err = ldpc::onchip_twoscan_launch(v, r, ch.onchip, code->sm_count, static_cast<const int8_t*>(llr), n_frames,
@@ -614,6 +626,68 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
                                      static_cast<int16_t*>(llr_out), st);
   }
   if (err != cudaSuccess) return cuda_fail(err, "ldpc_decode_batch launch");
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_qc_expand(const ldpc_qc_desc* qc, int32_t* row_ptr, int32_t* col_idx, int64_t capacity,
+                           int32_t* n_edges) {
+  g_last_error.clear();
+  if (qc == nullptr || qc->shift == nullptr) return fail(LDPC_ERR_INVALID_ARG, "qc and qc->shift must be non-NULL");
+  const int64_t mb = qc->base_rows, nb = qc->base_cols, z = qc->lift;
+  if (mb < 1 || nb < 1 || z < 1) return fail(LDPC_ERR_INVALID_ARG, "base_rows, base_cols and lift must be >= 1");
+  if (nb * z > INT32_MAX || mb * z + 1 > INT32_MAX)
+    return fail(LDPC_ERR_INVALID_ARG, "%lld x %lld blocks of %lld exceed int32 sizes", (long long)mb, (long long)nb,
+                (long long)z);
+  int64_t E = 0;
+  for (int64_t i = 0; i < mb * nb; ++i) {
+    const int32_t sh = qc->shift[i];
+    if (sh < -1 || sh >= z)
+      return fail(LDPC_ERR_INVALID_ARG, "shift[%lld] = %d is neither -1 nor in [0, %lld)", (long long)i, sh,
+                  (long long)z);
+    if (sh >= 0) E += z;
+  }
+  if (E > INT32_MAX) return fail(LDPC_ERR_INVALID_ARG, "%lld edges exceed int32", (long long)E);
+  if (col_idx != nullptr && capacity < E)
+    return fail(LDPC_ERR_INVALID_ARG, "col_idx holds %lld entries, %lld needed", (long long)capacity, (long long)E);
+  if (n_edges != nullptr) *n_edges = (int32_t)E;
+  int64_t e = 0;
+  for (int64_t i = 0; i < mb; ++i) {
+    for (int64_t r = 0; r < z; ++r) {
+      if (row_ptr != nullptr) row_ptr[i * z + r] = (int32_t)e;
+      for (int64_t j = 0; j < nb; ++j) {
+        const int32_t sh = qc->shift[i * nb + j];
+        if (sh < 0) continue;
+        if (col_idx != nullptr) col_idx[e] = (int32_t)(j * z + (r + sh) % z);
+        ++e;
+      }
+    }
+  }
+  if (row_ptr != nullptr) row_ptr[mb * z] = (int32_t)e;
+  return LDPC_OK;
+}
+
+ldpc_status ldpc_code_create_qc(ldpc_code** out, const ldpc_qc_desc* qc, int device) {
+  if (out == nullptr) return fail(LDPC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int32_t E = 0;
+  ldpc_status s = ldpc_qc_expand(qc, nullptr, nullptr, 0, &E);
+  if (s != LDPC_OK) return s;
+  const int32_t M = qc->base_rows * qc->lift, N = qc->base_cols * qc->lift;
+  std::vector<int32_t> rp((size_t)M + 1), ci((size_t)E);
+  s = ldpc_qc_expand(qc, rp.data(), ci.data(), E, nullptr);
+  if (s != LDPC_OK) return s;
+  ldpc_code* c = nullptr;
+  s = ldpc_code_create(&c, N, M, rp.data(), ci.data(), device);
+  if (s != LDPC_OK) return s;
+  std::vector<int32_t> layer((size_t)M);
+  for (int32_t m = 0; m < M; ++m) layer[(size_t)m] = m / qc->lift;
+  s = ldpc_code_set_layers(c, qc->base_rows, layer.data());
+  if (s != LDPC_OK) {
+    const std::string why = g_last_error;
+    ldpc_code_destroy(c);
+    return fail(s, "block-row layers: %s", why.c_str());
+  }
+  *out = c;
   return LDPC_OK;
 }
 
@@ -828,6 +902,7 @@ ldpc_status ldpc_decode_batch_noalloc(const ldpc_code* code, const ldpc_decode_p
   r.num = params->norm_num;
   r.shift = params->norm_shift;
   r.qm = params->msg_sat;
+  r.psat = params->posterior == LDPC_POSTERIOR_SAT8 ? 127 : 0;
   // every buffer the decoder reads before writing is initialised by the decoder
   // itself (state memset, init kernel), so contents left by a previous call do not matter
   const cudaError_t err = ldpc::stream_int8_decode(view(code), r, form, L, scratch, code->sm_count,

@@ -407,6 +407,7 @@ cudaError_t launch_plan(const ldpc_multi* p, void* ws, cudaStream_t st) {
     r.num = jb.params.norm_num;
     r.shift = jb.params.norm_shift;
     r.qm = jb.params.msg_sat;
+    r.psat = 0;
     if (sj.pingpong)
       e = ldpc::pingpong_int8_decode(view(jb.code), r, p->form, sj.pp, static_cast<char*>(ws) + sj.offset, jb.llr,
                                      jb.n_frames, jb.params.max_iter, jb.params.early_stop, jb.hard_bits,
@@ -508,9 +509,9 @@ ldpc_status ldpc_multi_create(ldpc_multi** out, const ldpc_multi_job* jobs, int3
     else if ((s = check_params(jb.code, &jb.params)) != LDPC_OK) fail(s, "job %d: %s", j, ldpc_last_error());
     else if (jb.params.dtype != LDPC_DTYPE_INT8 ||
              (jb.params.form != LDPC_FORM_SS_FIXED && jb.params.form != LDPC_FORM_SS_1BIT) ||
-             jb.params.schedule != LDPC_SCHEDULE_FLOODING)
+             jb.params.schedule != LDPC_SCHEDULE_FLOODING || jb.params.posterior != LDPC_POSTERIOR_EXACT)
       s = fail(LDPC_ERR_UNSUPPORTED, "job %d: batches run int8 single-scan decodes (SS_FIXED or SS_1BIT, flooding "
-               "schedule)", j);
+               "schedule, exact posterior)", j);
     else if (form >= 0 && jb.params.form != form)
       s = fail(LDPC_ERR_INVALID_ARG, "job %d: every job of a batch must use the same form", j);
     else if (device >= 0 && jb.code->device != device)

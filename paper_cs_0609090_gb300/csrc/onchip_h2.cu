@@ -23,6 +23,8 @@
 //   form 0 (Section IV): [E][P] u16: L + 128 per frame (one byte each)
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "h2_body.cuh"
 #include "kernels.h"
 #include "launch_util.h"
@@ -157,30 +159,38 @@ onchip_h2_kernel(const DevCode c, const IntRule r, const int8_t* __restrict__ ll
       // without early stop every valid frame continues; the lanes of a missing
       // frame (an odd batch) hold values nobody reads
       const bool all = !ES || cont == (1u << G) - 1u;
-      for (int n = tid; n < N; n += nt) {
-        uint32_t w[P];
-        if (!all) ld_pairs<G>(Zs, n, w);
+      // the 8-bit posterior (r.psat > 0) stores Z^(k) clamped; the choice is
+      // made once per pass, so the exact decode runs the pass without it
+      const auto col_pass = [&](auto clamp) {
+        for (int n = tid; n < N; n += nt) {
+          uint32_t w[P];
+          if (!all) ld_pairs<G>(Zs, n, w);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const uint32_t zz = acc_to_pair(Acc[(size_t)n * P + p]);
-          const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
-          if (all) {
-            w[p] = h;
-          } else {
-            const uint32_t sel = (((cont >> (2 * p)) & 1u) ? 0x0000ffffu : 0u) |
-                                 (((cont >> (2 * p + 1)) & 1u) ? 0xffff0000u : 0u);
-            w[p] = (h & sel) | (w[p] & ~sel);
+          for (int p = 0; p < P; ++p) {
+            const uint32_t zz = acc_to_pair(Acc[(size_t)n * P + p]);
+            uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
+            if constexpr (decltype(clamp)::value)
+              h = hmin(hmax(h, ints_to_h2(-r.psat, -r.psat)), ints_to_h2(r.psat, r.psat));
+            if (all) {
+              w[p] = h;
+            } else {
+              const uint32_t sel = (((cont >> (2 * p)) & 1u) ? 0x0000ffffu : 0u) |
+                                   (((cont >> (2 * p + 1)) & 1u) ? 0xffff0000u : 0u);
+              w[p] = (h & sel) | (w[p] & ~sel);
+            }
+            if constexpr (RSET) {
+              Acc[(size_t)n * P + p] = Rs[(size_t)n * P + p];
+            } else {
+              const uint32_t bias = (uint32_t)__ldg(c.cdeg + n) * 0x66006600u;
+              const int32_t lo = q0v(llr, N, f0 + 2 * p, F, n), hi = q0v(llr, N, f0 + 2 * p + 1, F, n);
+              Acc[(size_t)n * P + p] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
+            }
           }
-          if constexpr (RSET) {
-            Acc[(size_t)n * P + p] = Rs[(size_t)n * P + p];
-          } else {
-            const uint32_t bias = (uint32_t)__ldg(c.cdeg + n) * 0x66006600u;
-            const int32_t lo = q0v(llr, N, f0 + 2 * p, F, n), hi = q0v(llr, N, f0 + 2 * p + 1, F, n);
-            Acc[(size_t)n * P + p] = (int32_t)((uint32_t)acc_pack(lo, hi) - bias);
-          }
+          st_pairs<G>(Zs, n, w);
         }
-        st_pairs<G>(Zs, n, w);
-      }
+      };
+      if (r.psat > 0) col_pass(std::true_type{});
+      else col_pass(std::false_type{});
       if (ES) {
         if (tid < G && ((stop >> tid) & 1u)) s_iters[tid] = k - 1;
         if (tid == 0) s_ok |= stop;

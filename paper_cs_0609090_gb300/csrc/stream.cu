@@ -77,6 +77,7 @@ struct H2S {
   int32_t* iters;  // [2 FP]: frame 2p + b
   uint32_t* ok;    // [FP]
   int FP;
+  int psat;        // > 0: the stored posterior Zs is clamped to [-psat, psat]; 0: exact
 };
 
 H2S h2s_view(void* ws, const StreamLayout& L) {
@@ -92,6 +93,7 @@ H2S h2s_view(void* ws, const StreamLayout& L) {
   s.iters = reinterpret_cast<int32_t*>(b + L.iters);
   s.ok = reinterpret_cast<uint32_t*>(b + L.ok);
   s.FP = L.lanes;
+  s.psat = 0;
   return s;
 }
 
@@ -321,9 +323,13 @@ __global__ void __launch_bounds__(256) h2s_cols4(const DevCode c, H2S s, int k) 
   const uint4 sel = make_uint4(selm(cont.x), selm(cont.y), selm(cont.z), selm(cont.w));
   const bool all = (sel.x & sel.y & sel.z & sel.w) == 0xffffffffu;
   const bool any = (cont.x | cont.y | cont.z | cont.w) != 0u;
-  auto conv = [](uint32_t a) {
+  // the 8-bit posterior stores Z^(k) clamped (the accumulator stays exact)
+  const uint32_t sat2 = ints_to_h2(s.psat, s.psat), nsat2 = ints_to_h2(-s.psat, -s.psat);
+  const bool sat = s.psat > 0;
+  auto conv = [sat, sat2, nsat2](uint32_t a) {
     const uint32_t zz = acc_to_pair((int32_t)a);
-    return ints_to_h2(lo16(zz), hi16(zz));
+    const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
+    return sat ? hmin(hmax(h, nsat2), sat2) : h;
   };
   if (any) {
 #pragma unroll 4
@@ -365,10 +371,12 @@ __global__ void __launch_bounds__(256) h2s_cols(const DevCode c, H2S s, int k) {
   const uint32_t stop = ES ? (act & ~s.fail[cur * s.FP + p]) : 0u;
   const uint32_t cont = act & ~stop;
   const uint32_t sel = ((cont & 1u) ? 0x0000ffffu : 0u) | ((cont & 2u) ? 0xffff0000u : 0u);
+  const uint32_t sat2 = ints_to_h2(s.psat, s.psat), nsat2 = ints_to_h2(-s.psat, -s.psat);
   for (int n = blockIdx.x * 8 + (threadIdx.x >> 5); n < c.N; n += gridDim.x * 8) {
     const size_t o = (size_t)n * s.FP + p;
     const uint32_t zz = acc_to_pair(s.acc[o]);
-    const uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
+    uint32_t h = ints_to_h2(lo16(zz), hi16(zz));
+    if (s.psat > 0) h = hmin(hmax(h, nsat2), sat2);  // the 8-bit posterior
     s.z[o] = (h & sel) | (s.z[o] & ~sel);
     const uint32_t q = s.q0[o];
     s.acc[o] = (int32_t)((uint32_t)acc_pack((int32_t)(int8_t)(q & 0xffu), (int32_t)(int8_t)(q >> 8)) -
@@ -496,6 +504,7 @@ cudaError_t stream_int8_decode(const DevCode& c, const IntRule& r, int form, con
                                int sm_count, const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop,
                                uint8_t* bits, int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
   H2S s = h2s_view(ws, L);
+  s.psat = r.psat;
   const dim3 tgrid((c.N + 63) / 64, L.lanes / 32);
   // L^(0) = 0: Section V state all zero, per-edge bytes L + 128 = 0x80
   cudaError_t e0 = cudaMemsetAsync(static_cast<char*>(ws) + L.st, form == 1 ? 0 : 0x80, L.q0 - L.st, st);

@@ -33,6 +33,8 @@ RULES = {"plain": LDPC_RULE_PLAIN, "offset": LDPC_RULE_OFFSET, "normalized": LDP
  LDPC_KERNEL_PERSISTENT, LDPC_KERNEL_PINGPONG) = range(7)
 LDPC_SCHEDULE_FLOODING, LDPC_SCHEDULE_LAYERED = 0, 1
 SCHEDULES = {"flooding": LDPC_SCHEDULE_FLOODING, "layered": LDPC_SCHEDULE_LAYERED}
+LDPC_POSTERIOR_EXACT, LDPC_POSTERIOR_SAT8 = 0, 1
+POSTERIORS = {"exact": LDPC_POSTERIOR_EXACT, "sat8": LDPC_POSTERIOR_SAT8}
 KERNELS = {"auto": LDPC_KERNEL_AUTO, "onchip_int": LDPC_KERNEL_ONCHIP_INT, "onchip_half": LDPC_KERNEL_ONCHIP_HALF,
            "stream": LDPC_KERNEL_STREAM, "cluster": LDPC_KERNEL_CLUSTER, "persistent": LDPC_KERNEL_PERSISTENT,
            "pingpong": LDPC_KERNEL_PINGPONG}
@@ -44,7 +46,7 @@ EXPORTS = ("ldpc_code_create", "ldpc_code_destroy", "ldpc_code_info", "ldpc_work
            "ldpc_adam_step", "ldpc_awgn_llr_f32", "ldpc_quantize_llr", "ldpc_multi_create", "ldpc_multi_destroy",
            "ldpc_multi_workspace_size", "ldpc_multi_decode", "ldpc_multi_autotune", "ldpc_multi_info",
            "ldpc_code_layers", "ldpc_code_set_layers", "ldpc_wait_selftest", "ldpc_kernel_choice",
-           "ldpc_last_error")
+           "ldpc_qc_expand", "ldpc_code_create_qc", "ldpc_last_error")
 NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -59,7 +61,13 @@ class ldpc_decode_params(ctypes.Structure):
                 ("offset", ctypes.c_int32), ("norm_num", ctypes.c_int32), ("norm_shift", ctypes.c_int32),
                 ("offset_f32", ctypes.c_float), ("norm_f32", ctypes.c_float),
                 ("msg_sat", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("early_stop", ctypes.c_int32), ("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+                ("early_stop", ctypes.c_int32), ("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("posterior", ctypes.c_int32)]
+
+
+class ldpc_qc_desc(ctypes.Structure):
+    _fields_ = [("base_rows", ctypes.c_int32), ("base_cols", ctypes.c_int32), ("lift", ctypes.c_int32),
+                ("shift", ctypes.c_void_p)]
 
 
 class ldpc_multi_job(ctypes.Structure):
@@ -106,6 +114,8 @@ _lib.ldpc_multi_autotune.argtypes = [_P, _P, ctypes.c_size_t, ctypes.c_int32, _P
 _lib.ldpc_multi_info.argtypes = [_P, ctypes.POINTER(ldpc_multi_tuning), _P, _P, _P, _P, _P]
 _lib.ldpc_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_int32]
 _lib.ldpc_kernel_choice.argtypes = [_P, ctypes.POINTER(ldpc_decode_params), ctypes.c_int32, _P]
+_lib.ldpc_qc_expand.argtypes = [ctypes.POINTER(ldpc_qc_desc), _P, _P, ctypes.c_int64, _P]
+_lib.ldpc_code_create_qc.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(ldpc_qc_desc), ctypes.c_int]
 _lib.ldpc_last_error.restype = ctypes.c_char_p
 for _f in EXPORTS[:-1]:
     getattr(_lib, _f).restype = ctypes.c_int32
@@ -153,9 +163,10 @@ def ldpc_last_error() -> str:
 
 def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=3, norm_shift=2,
                 offset_f32=0.0, norm_f32=0.75, msg_sat=127, max_iter=20, early_stop=1,
-                norm=None, kernel="auto", schedule="flooding", **_ignored) -> ldpc_decode_params:
+                norm=None, kernel="auto", schedule="flooding", posterior="exact", **_ignored) -> ldpc_decode_params:
     """Builds ldpc_decode_params from names ('int8'/'f32', 'ss_fixed'/'ss_1bit'/'two_scan'/'two_scan_1bit',
-    'plain'/'offset'/'normalized', 'flooding'/'layered').  ``norm`` is an alias for norm_f32."""
+    'plain'/'offset'/'normalized', 'flooding'/'layered', 'exact'/'sat8').  ``norm`` is an alias for
+    norm_f32."""
     if norm is not None:
         norm_f32 = norm
     return ldpc_decode_params(DTYPES[dtype] if isinstance(dtype, str) else dtype,
@@ -164,7 +175,8 @@ def make_params(dtype="int8", form="ss_1bit", rule="offset", offset=0, norm_num=
                               int(offset), int(norm_num), int(norm_shift), float(offset_f32),
                               float(norm_f32), int(msg_sat), int(max_iter), int(early_stop),
                               KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
-                              SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule))
+                              SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule),
+                              POSTERIORS[posterior] if isinstance(posterior, str) else int(posterior))
 
 
 def ldpc_code_create(n_vars: int, n_checks: int, row_ptr, col_idx, device: int = 0) -> int:
@@ -174,6 +186,32 @@ def ldpc_code_create(n_vars: int, n_checks: int, row_ptr, col_idx, device: int =
     h = _P()
     _check(_lib.ldpc_code_create(ctypes.byref(h), int(n_vars), int(n_checks), _ptr(rp), _ptr(ci), int(device)),
            "ldpc_code_create")
+    return h.value
+
+
+def _qc_desc(shifts, lift: int):
+    sh = np.ascontiguousarray(shifts, dtype=np.int32)
+    assert sh.ndim == 2
+    return ldpc_qc_desc(sh.shape[0], sh.shape[1], int(lift), sh.ctypes.data), sh
+
+
+def ldpc_qc_expand(shifts, lift: int):
+    """(row_ptr, col_idx) int32 of the quasi-cyclic code whose base matrix of
+    circulant shifts is ``shifts`` [mb, nb] (-1: zero block), lifted by ``lift``.
+    Host computation only."""
+    d, keep = _qc_desc(shifts, lift)
+    e = ctypes.c_int32()
+    _check(_lib.ldpc_qc_expand(ctypes.byref(d), None, None, 0, ctypes.byref(e)), "ldpc_qc_expand")
+    rp = np.zeros(d.base_rows * d.lift + 1, np.int32)
+    ci = np.zeros(max(e.value, 1), np.int32)
+    _check(_lib.ldpc_qc_expand(ctypes.byref(d), _ptr(rp), _ptr(ci), int(ci.size), None), "ldpc_qc_expand")
+    return rp, ci[:e.value]
+
+
+def ldpc_code_create_qc(shifts, lift: int, device: int = 0) -> int:
+    d, keep = _qc_desc(shifts, lift)
+    h = _P()
+    _check(_lib.ldpc_code_create_qc(ctypes.byref(h), ctypes.byref(d), int(device)), "ldpc_code_create_qc")
     return h.value
 
 
@@ -332,6 +370,17 @@ class Code:
         self.handle = ldpc_code_create(n_vars, n_checks, row_ptr, col_idx, device)
         self.n_vars, self.n_checks = int(n_vars), int(n_checks)
         self.device = device
+
+    @classmethod
+    def from_qc(cls, shifts, lift, device=0):
+        """A quasi-cyclic code from its base matrix of circulant shifts (-1: zero
+        block) and lift; its layers are the block rows."""
+        obj = cls.__new__(cls)
+        sh = np.asarray(shifts)
+        obj.handle = ldpc_code_create_qc(sh, lift, device)
+        obj.n_vars, obj.n_checks = int(sh.shape[1] * lift), int(sh.shape[0] * lift)
+        obj.device = device
+        return obj
 
     @classmethod
     def from_inputs(cls, code, device=0):

@@ -26,7 +26,8 @@ def oracle_int(code, q0, form, p):
     return oracle.decode_int(code, q0.astype(np.int32), form=form, rule=p.get("rule", "offset"),
                              offset=p.get("offset", 0), norm_num=p.get("norm_num", 3),
                              norm_shift=p.get("norm_shift", 2), msg_sat=p.get("msg_sat", 127),
-                             max_iter=p["max_iter"], early_stop=p.get("early_stop", 1))
+                             max_iter=p["max_iter"], early_stop=p.get("early_stop", 1),
+                             post_sat=127 if p.get("posterior", "exact") == "sat8" else 0)
 
 
 def assert_int_parity(g, o):

@@ -39,7 +39,7 @@ def test_struct_layouts_match_the_header(L, tmp_path):
     header with gcc, equal the binding's ctypes definitions."""
     import subprocess
     structs = {"ldpc_decode_params": L.ldpc_decode_params, "ldpc_multi_job": L.ldpc_multi_job,
-               "ldpc_multi_tuning": L.ldpc_multi_tuning}
+               "ldpc_multi_tuning": L.ldpc_multi_tuning, "ldpc_qc_desc": L.ldpc_qc_desc}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ldpc_gb300.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
@@ -106,3 +106,32 @@ def test_valid_code_without_gpu_reports_cuda_error(L):
 def test_unpack_bits_layout(L):
     hb = np.array([[0b00000101, 0b1]], dtype=np.uint8)
     assert L.unpack_bits(hb, 9).tolist() == [[1, 0, 1, 0, 0, 0, 0, 0, 1]]
+
+
+def test_qc_expand_matches_the_generator(L):
+    """ldpc_qc_expand (host code of the library) rebuilds the N=7493 QC code
+    from its base matrix of shifts, and small hand-checked cases: one circulant
+    row r -> column (r + s) mod z, zero blocks skipped."""
+    from paper_cs_0609090_gb300 import inputs as I
+    code = I.make_workload("qc_n7493", n_frames=1).code
+    rp, ci = L.ldpc_qc_expand(code.meta["shifts"], code.meta["Z"])
+    assert np.array_equal(rp, code.row_ptr) and np.array_equal(ci, code.col_idx)
+    rp, ci = L.ldpc_qc_expand([[1, -1, 0]], 3)
+    assert rp.tolist() == [0, 2, 4, 6]
+    assert ci.tolist() == [1, 6, 2, 7, 0, 8]
+    rp, ci = L.ldpc_qc_expand([[-1, -1]], 4)
+    assert rp.tolist() == [0, 0, 0, 0, 0] and ci.size == 0
+
+
+def test_qc_expand_rejects_malformed_descriptors(L):
+    for shifts, z in (([[3]], 3), ([[-2]], 3), ([[0]], 0)):
+        with pytest.raises(L.LdpcError):
+            L.ldpc_qc_expand(shifts, z)
+    d, keep = L._qc_desc([[0, 1]], 4)
+    rp = np.zeros(5, np.int32)
+    ci = np.zeros(7, np.int32)  # 8 needed
+    st = L._lib.ldpc_qc_expand(ctypes.byref(d), rp.ctypes.data_as(ctypes.c_void_p),
+                               ci.ctypes.data_as(ctypes.c_void_p), 7, None)
+    assert st == L.LDPC_ERR_INVALID_ARG and "needed" in L.ldpc_last_error()
+    assert L._lib.ldpc_qc_expand(None, None, None, 0, None) == L.LDPC_ERR_INVALID_ARG
+
