@@ -134,6 +134,9 @@ struct PingpongLayout {
   size_t zb = 0, st = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
 };
 PingpongLayout pingpong_layout(int form, int N, int M, int ell_w, int F);
+// Sets the ping-pong row kernels' shared-memory attribute on the current
+// device (once per device, outside stream capture).
+cudaError_t pingpong_prepare();
 bool pingpong_int8_eligible(int N, int M, int ell_w, int max_row_deg, int max_col_deg, int qm, int form, int F);
 cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, const PingpongLayout& L, void* ws,
                                  const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,

@@ -441,6 +441,12 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
     ldpc_code_destroy(c);
     return cs;
   }
+  // kernel attributes of this device, set here: code creation is never inside
+  // a stream capture, and every decode of the code runs on this device
+  if ((err = ldpc::pingpong_prepare()) != cudaSuccess) {
+    ldpc_code_destroy(c);
+    return cuda_fail(err, "ldpc_code_create kernel attributes");
+  }
   // default layers for the layered schedule: checks in row order, each into the
   // lowest layer none of whose checks shares a variable with it
   c->pos = pos;

@@ -44,9 +44,26 @@ namespace {
 #endif
 
 constexpr uint32_t kFull = 0xffffffffu;
+#ifndef LDPC_PP2_STAGES
+#define LDPC_PP2_STAGES 2
+#endif
+#ifndef LDPC_PP2_GROUPS
+#define LDPC_PP2_GROUPS 1
+#endif
+#ifndef LDPC_PP2_MINB1
+#define LDPC_PP2_MINB1 4
+#endif
+#ifndef LDPC_PP2_UNROLL
+#define LDPC_PP2_UNROLL 4
+#endif
+
 constexpr int kWarps = 8;   // per block
-constexpr int kRows = 4;    // checks per warp
+constexpr int kRows = 4;    // checks per handle group (kRows x degree <= 32 lanes)
 constexpr int kTile = kWarps * kRows;
+constexpr int kStages = LDPC_PP2_STAGES;  // staged checks in flight + 1
+constexpr int kGroups = LDPC_PP2_GROUPS;  // handle groups per warp in the row kernel
+constexpr int kRowTile = kTile * kGroups;  // checks per row-kernel block
+constexpr int kUnroll = LDPC_PP2_UNROLL;   // unrolling of the staged check loop
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -214,57 +231,67 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
 }
 
 // Per-warp staging of the Section V checks of uniform degree D <= 7: the
-// inputs of check r + 1 (D posterior pairs and both state words per lane) are
-// copied into shared memory while check r computes, so that the gathers'
-// latency overlaps the arithmetic instead of stalling it.  Measured on the
-// N=64800 code (1024 frames, 50 iterations, same GB300): 8.13 ms against
-// 8.73 ms with the inputs read straight from global memory.
+// inputs of the checks kStages - 1 ahead (D posterior pairs and both state
+// words per lane) are copied into shared memory while the current check
+// computes, so that the gathers' latency overlaps the arithmetic instead of
+// stalling it.  A warp takes kGroups groups of kRows checks (one lane-held
+// handle word per group).  Measured on the N=64800 code (1024 frames, 50
+// iterations, same GB300), two stages, one group: 8.13 ms against 8.73 ms with
+// the inputs read straight from global memory; three stages 8.87 ms, two
+// groups 8.35 ms, four groups 13.1 ms; the loop unrolled 1 or 2 times instead
+// of 4: +1.6 % / +1.3 %.
 struct Stage {
-  uint2 z[2][7][32];
-  uint4 s[2][2][32];
+  uint2 z[kStages][7][32];
+  uint4 s[kStages][2][32];
 };
+constexpr size_t kStageBytes = sizeof(Stage) * kWarps;
 
 template <bool ES, int D>
-__device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, uint32_t hl, int lane, Stage& sg) {
-  const auto issue = [&](int r, int b) {
+__device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const uint32_t* hl, int lane, Stage& sg) {
+  constexpr int T = kRows * kGroups;
+  const auto issue = [&](int t) {
+    const int b = t % kStages, g = t / kRows, r = t - g * kRows;
 #pragma unroll
-    for (int j = 0; j < D; ++j) cp_async8(&sg.z[b][j][lane], x.Zr + __shfl_sync(kFull, hl, r * D + j));
-    const size_t so = (size_t)(m0 + r) * x.FP * 8;
+    for (int j = 0; j < D; ++j) cp_async8(&sg.z[b][j][lane], x.Zr + __shfl_sync(kFull, hl[g], r * D + j));
+    const size_t so = (size_t)(m0 + t) * x.FP * 8;
     cp_async16(&sg.s[b][0][lane], x.S1 + so);
     cp_async16(&sg.s[b][1][lane], x.S2 + so);
-    cp_async_commit();
   };
   uint32_t fail = 0;
-  issue(0, 0);
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    const int b = r & 1;
-    if (r + 1 < kRows) {
-      issue(r + 1, b ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+  for (int t = 0; t < kStages - 1; ++t) {
+    if (t < T) issue(t);
+    cp_async_commit();
+  }
+#pragma unroll kUnroll
+  for (int t = 0; t < T; ++t) {
+    // one group is committed per check (empty past the end), so waiting for
+    // all but the newest kStages - 1 groups completes check t's copies
+    if (t + kStages - 1 < T) issue(t + kStages - 1);
+    cp_async_commit();
+    cp_async_wait<kStages - 1>();
+    const int b = t % kStages, g = t / kRows, r = t - g * kRows;
     uint32_t h[D], wa[D], wb[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      h[j] = __shfl_sync(kFull, hl, r * D + j);
+      h[j] = __shfl_sync(kFull, hl[g], r * D + j);
       const uint2 v = sg.z[b][j][lane];
       wa[j] = v.x;
       wb[j] = v.y;
     }
-    fail |= check2_sv<ES, D>(x, m0 + r, D, h, wa, wb, sg.s[b][0][lane], sg.s[b][1][lane]);
+    fail |= check2_sv<ES, D>(x, m0 + t, D, h, wa, wb, sg.s[b][0][lane], sg.s[b][1][lane]);
   }
   return fail;
 }
 
-// Row kernel of iteration k: block (bx, chunk) takes kTile checks of the
-// degree-sorted order for the chunk's 64 pairs (warp w: checks bx kTile + w kRows
-// ..., lane l: pairs chunk 64 + 2 l, + 1).
+// Row kernel of iteration k: block (bx, chunk) takes kRowTile checks of the
+// degree-sorted order for the chunk's 64 pairs (warp w: checks bx kRowTile + w
+// kRows kGroups ..., lane l: pairs chunk 64 + 2 l, + 1).
 template <int FORM, bool ES>
 // CTAs per SM (registers 65536 / (256 x this)), measured on the N=64800 code:
-// Section V 3 (8.68 ms; 4 spills and gives 8.77), per edge 4 (11.99 against 12.38)
-__global__ void __launch_bounds__(kWarps * 32, FORM == 1 ? 3 : 4) pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
+// Section V with staged inputs 4 (7.83 ms, 52 bytes of spills, against 8.16 ms
+// at 3 without spills; 5 spills 436 bytes), per edge 4 (11.99 against 12.38)
+__global__ void __launch_bounds__(kWarps * 32, FORM == 1 ? LDPC_PP2_MINB1 : 4) pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.y * 64 + 2 * lane;
   const int FP = s.FP;
@@ -302,35 +329,42 @@ __global__ void __launch_bounds__(kWarps * 32, FORM == 1 ? 3 : 4) pp2_rows(const
   x.rule = make_h2rule(ir);
   // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
   x.ksat = hfma(ints_to_h2(ir.qm, ir.qm), h2c_q11(16), h2c_q11(15));
-  const int m0 = blockIdx.x * kTile + warp * kRows;
-  const int nr = min(kRows, c.M - m0);
+  const int m0 = blockIdx.x * kRowTile + warp * kRows * kGroups;
+  const int nr = min(kRows * kGroups, c.M - m0);
   if (nr <= 0) return;
   uint32_t fail = 0;
   const int d0 = c.deg(m0);
-  if (nr == kRows && d0 == c.deg(m0 + nr - 1) && (d0 == 6 || d0 == 7)) {
-    // lane l < kRows d0 holds the handle of (check m0 + l / d0, position l % d0)
-    uint32_t hl = 0;
-    if (lane < kRows * d0) {
-      const int r = lane / d0, j = lane - r * d0;
-      hl = (uint32_t)c.col(j, m0 + r) * x.FP;
+  if (nr == kRows * kGroups && d0 == c.deg(m0 + nr - 1) && (d0 == 6 || d0 == 7)) {
+    // lane l < kRows d0 of group g holds the handle of (check m0 + g kRows +
+    // l / d0, position l % d0)
+    uint32_t hl[kGroups];
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+      hl[g] = 0;
+      if (lane < kRows * d0) {
+        const int r = lane / d0, j = lane - r * d0;
+        hl[g] = (uint32_t)c.col(j, m0 + g * kRows + r) * x.FP;
+      }
     }
 #if LDPC_PP2_STAGED
     if constexpr (FORM == 1) {
-      __shared__ Stage stage[kWarps];
-      fail = d0 == 6 ? rows_staged<ES, 6>(x, m0, hl, lane, stage[warp]) : rows_staged<ES, 7>(x, m0, hl, lane, stage[warp]);
+      extern __shared__ __align__(16) unsigned char pp2_smem[];
+      Stage& sg = reinterpret_cast<Stage*>(pp2_smem)[warp];
+      fail = d0 == 6 ? rows_staged<ES, 6>(x, m0, hl, lane, sg) : rows_staged<ES, 7>(x, m0, hl, lane, sg);
     } else
 #endif
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
+    for (int t = 0; t < kRows * kGroups; ++t) {
+      const int g = t / kRows, r = t - g * kRows;
       uint32_t h[8];
       if (d0 == 6) {
 #pragma unroll
-        for (int j = 0; j < 6; ++j) h[j] = __shfl_sync(kFull, hl, r * 6 + j);
-        fail |= check2<FORM, ES, 6>(x, m0 + r, 6, h);
+        for (int j = 0; j < 6; ++j) h[j] = __shfl_sync(kFull, hl[g], r * 6 + j);
+        fail |= check2<FORM, ES, 6>(x, m0 + t, 6, h);
       } else {
 #pragma unroll
-        for (int j = 0; j < 7; ++j) h[j] = __shfl_sync(kFull, hl, r * 7 + j);
-        fail |= check2<FORM, ES, 7>(x, m0 + r, 7, h);
+        for (int j = 0; j < 7; ++j) h[j] = __shfl_sync(kFull, hl[g], r * 7 + j);
+        fail |= check2<FORM, ES, 7>(x, m0 + t, 7, h);
       }
     }
   } else {
@@ -521,14 +555,26 @@ cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, const int8
                     int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
   const dim3 tgrid((unsigned)((c.N + 63) / 64), (unsigned)(s.FP / 32));
   const dim3 rgrid((unsigned)((c.M + kTile - 1) / kTile), (unsigned)(s.FP / 64));
+  const dim3 rgrid_rows((unsigned)((c.M + kRowTile - 1) / kRowTile), (unsigned)(s.FP / 64));
   pp2_init<ES><<<tgrid, 256, 0, st>>>(c, llr, s, K);
-  for (int k = 1; k <= K; ++k) pp2_rows<FORM, ES><<<rgrid, kWarps * 32, 0, st>>>(c, r, s, k);
+  const size_t smem = FORM == 1 && LDPC_PP2_STAGED ? kStageBytes : 0;
+  for (int k = 1; k <= K; ++k) pp2_rows<FORM, ES><<<rgrid_rows, kWarps * 32, smem, st>>>(c, r, s, k);
   pp2_final<ES><<<rgrid, kWarps * 32, 0, st>>>(c, s, K);
   pp2_output<<<tgrid, 256, 0, st>>>(c, s, K, bits, iters, ok, zout);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t pingpong_prepare() {
+  // the staged Section V row kernels take kStageBytes of dynamic shared memory;
+  // set on the current device outside any stream capture (code creation)
+  for (auto f : {pp2_rows<1, false>, pp2_rows<1, true>}) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 PingpongLayout pingpong_layout(int form, int N, int M, int ell_w, int F) {
   PingpongLayout L;
