@@ -53,6 +53,9 @@ constexpr uint32_t kFull = 0xffffffffu;
 #ifndef LDPC_PP2_MINB1
 #define LDPC_PP2_MINB1 4
 #endif
+#ifndef LDPC_PP2_SHIFT_FMA
+#define LDPC_PP2_SHIFT_FMA 1
+#endif
 #ifndef LDPC_PP2_UNROLL
 #define LDPC_PP2_UNROLL 4
 #endif
@@ -64,6 +67,8 @@ constexpr int kStages = LDPC_PP2_STAGES;  // staged checks in flight + 1
 constexpr int kGroups = LDPC_PP2_GROUPS;  // handle groups per warp in the row kernel
 constexpr int kRowTile = kTile * kGroups;  // checks per row-kernel block
 constexpr int kUnroll = LDPC_PP2_UNROLL;   // unrolling of the staged check loop
+// sign-word doubling as a multiply (N=64800, same GB300: 7.617 against 7.653 ms)
+constexpr bool kShiftFma = LDPC_PP2_SHIFT_FMA != 0;
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -75,6 +80,7 @@ struct PP2 {
   int32_t* iters;  // [2 FP]
   uint32_t* okw;   // [FP]
   int32_t F, FP, rows, ub;
+  uint32_t two;    // 2 (a value the compiler cannot fold; see sv_pass1)
 };
 
 __device__ __forceinline__ uint32_t half_mask(uint32_t b) {
@@ -97,11 +103,11 @@ struct Delta {
   uint32_t Ao, Do, Io, SO;  // iteration k-2
   __device__ __forceinline__ Delta(const NewState& n, const SV& o)
       : An(n.An), Dn(hsub(n.Bn, n.An)), In(n.In), SN(n.Sn), Ao(o.A), Do(hsub(o.B, o.A)), Io(o.I), SO(o.S) {}
-  __device__ __forceinline__ uint32_t next(int j) {
+  __device__ __forceinline__ uint32_t next(int j, uint32_t two) {
     const uint32_t Ln = hfma(Dn, heq_one(In, h2c(j)), An) ^ (SN & 0x80008000u);
     const uint32_t Lo = hfma(Do, heq_one(Io, h2c(j)), Ao) ^ (SO & 0x80008000u);
-    SN += SN;
-    SO += SO;
+    SN *= two;
+    SO *= two;
     return hsub(Ln, Lo);
   }
 };
@@ -133,6 +139,7 @@ struct RowArgs {
   uint32_t FP, M;
   uint32_t amA, amB;   // running halves of the lane's two pairs
   uint32_t ksat;
+  uint32_t two;        // 2, doubling the running sign words (see sv_pass1)
   H2Rule rule;
 };
 
@@ -145,15 +152,21 @@ __device__ __forceinline__ uint32_t check2_sv(const RowArgs& x, int m, int d, co
                                               const uint32_t* wb, uint4 s1, uint4 s2) {
   constexpr int NJ = D > 0 ? D : 8;
   uint32_t pa = 0, pb = 0;
-  const NewState na = sv_pass1<D, 8, ES>(wa, d, SVUnit<true>::unpack(make_uint2(s1.x, s1.y)), x.rule, x.ksat, pa);
-  const NewState nb = sv_pass1<D, 8, ES>(wb, d, SVUnit<true>::unpack(make_uint2(s1.z, s1.w)), x.rule, x.ksat, pb);
+  const uint32_t two = kShiftFma ? x.two : 2u;
+  const NewState na =
+      sv_pass1<D, 8, ES>(wa, d, SVUnit<true>::unpack(make_uint2(s1.x, s1.y)), x.rule, x.ksat, pa, two);
+  const NewState nb =
+      sv_pass1<D, 8, ES>(wb, d, SVUnit<true>::unpack(make_uint2(s1.z, s1.w)), x.rule, x.ksat, pb, two);
   Delta ga(na, SVUnit<true>::unpack(make_uint2(s2.x, s2.y)));
   Delta gb(nb, SVUnit<true>::unpack(make_uint2(s2.z, s2.w)));
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     if (D > 0 || j < d) {
-      const uint32_t da = ga.next(j) & x.amA, db = gb.next(j) & x.amB;
-      if ((x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
+      // without early stop no frame is ever masked: the lanes past the batch
+      // decode all-zero channel values (exact zeros throughout) that no output reads
+      const uint32_t da = ES ? ga.next(j, two) & x.amA : ga.next(j, two);
+      const uint32_t db = ES ? gb.next(j, two) & x.amB : gb.next(j, two);
+      if (!ES || (x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
     }
   }
   const uint2 ua = pack_c8(na), ub = pack_c8(nb);
@@ -216,9 +229,9 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
         const uint32_t Lb = hfma(Dnb, heq_one(nb.In, h2c(j)), nb.An) ^ (SNb & 0x80008000u);
         SNa += SNa;
         SNb += SNb;
-        const uint32_t da = hsub(La, pe_to_h2(l2[j] & 0xffffu)) & x.amA;
-        const uint32_t db = hsub(Lb, pe_to_h2(l2[j] >> 16)) & x.amB;
-        if ((x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
+        const uint32_t da = ES ? hsub(La, pe_to_h2(l2[j] & 0xffffu)) & x.amA : hsub(La, pe_to_h2(l2[j] & 0xffffu));
+        const uint32_t db = ES ? hsub(Lb, pe_to_h2(l2[j] >> 16)) & x.amB : hsub(Lb, pe_to_h2(l2[j] >> 16));
+        if (!ES || (x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
         __stcg(reinterpret_cast<uint32_t*>(x.S2 + (size_t)(j * x.M + m) * x.FP * 2), h2_to_pe(La) | (h2_to_pe(Lb) << 16));
       }
     }
@@ -329,6 +342,7 @@ __global__ void __launch_bounds__(kWarps * 32, FORM == 1 ? LDPC_PP2_MINB1 : 4) p
   x.rule = make_h2rule(ir);
   // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
   x.ksat = hfma(ints_to_h2(ir.qm, ir.qm), h2c_q11(16), h2c_q11(15));
+  x.two = s.two;
   const int m0 = blockIdx.x * kRowTile + warp * kRows * kGroups;
   const int nr = min(kRows * kGroups, c.M - m0);
   if (nr <= 0) return;
@@ -615,6 +629,7 @@ cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, c
   s.FP = L.lanes;
   s.rows = L.rows;
   s.ub = L.ub;
+  s.two = 2u;
   // L^(0) = L^(-1) = 0: Section V state all zero, per-edge bytes L + 128 = 0x80
   cudaError_t e = cudaMemsetAsync(b + L.st, form == 1 ? 0 : 0x80, L.act - L.st, st);
   if (e != cudaSuccess) return e;

@@ -75,9 +75,12 @@ __device__ __forceinline__ void key_step(uint32_t u, int j, uint32_t& K1, uint32
 // state of iteration k-1; returns the minima, the first argmin and the signs
 // (as new state) and, in par, the decision parity of x^(k-1) (bit 0 even frame,
 // bit 1 odd frame).
+// `two` doubles the running sign word (x * two, two = 2): a constant lets the
+// compiler shift or add; a value it cannot see (a kernel argument) makes it an
+// integer multiply, which runs on the FMA pipe instead of the ALU pipe.
 template <int D, int DMAX, bool ES>
 __device__ __forceinline__ NewState sv_pass1(const uint32_t* w, int d, const SV& o1, const H2Rule& rule,
-                                             uint32_t ksat, uint32_t& par) {
+                                             uint32_t ksat, uint32_t& par, uint32_t two = 2u) {
   constexpr int NJ = D > 0 ? D : DMAX;
   uint32_t K1 = ksat, K2 = ksat, NEG = 0, Y = 0, SR = o1.S;
   const uint32_t D1 = hsub(o1.B, o1.A);
@@ -86,7 +89,7 @@ __device__ __forceinline__ NewState sv_pass1(const uint32_t* w, int d, const SV&
     if (D > 0 || j < d) {
       // f(A, B, n, n~) = A + (B - A) [j = n~], the sign s_mn on the binary16 sign bit
       const uint32_t L = hfma(D1, heq_one(o1.I, h2c(j)), o1.A) ^ (SR & 0x80008000u);
-      SR += SR;
+      SR *= two;
       const uint32_t u = hsub(w[j], L);
       if (ES) Y ^= dec_bits(w[j]);
       key_step(u, j, K1, K2, NEG);
