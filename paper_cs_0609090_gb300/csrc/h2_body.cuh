@@ -216,7 +216,9 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
         // 2^-11, so the minima come out as 16 min(|u|, Qm) + j; where both
         // are saturated A = B and the position of the first does not matter
         const uint32_t key = hfma_sat(hab(u), h2c_q11(16), h2c_q11(j));
-        K2[p] = hmin(K2[p], hmax(K1[p], key));
+        // at j = 0 the second minimum stays the start value: every key is at
+        // most 1, so min(ksat, max(ksat, key)) = ksat
+        if (j != 0) K2[p] = hmin(K2[p], hmax(K1[p], key));
         K1[p] = hmin(K1[p], key);
       }
     }

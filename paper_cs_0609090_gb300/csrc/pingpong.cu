@@ -56,6 +56,9 @@ constexpr uint32_t kFull = 0xffffffffu;
 #ifndef LDPC_PP2_SHIFT_FMA
 #define LDPC_PP2_SHIFT_FMA 1
 #endif
+#ifndef LDPC_PP2_EQ_FMA
+#define LDPC_PP2_EQ_FMA 0
+#endif
 #ifndef LDPC_PP2_UNROLL
 #define LDPC_PP2_UNROLL 4
 #endif
@@ -69,6 +72,9 @@ constexpr int kRowTile = kTile * kGroups;  // checks per row-kernel block
 constexpr int kUnroll = LDPC_PP2_UNROLL;   // unrolling of the staged check loop
 // sign-word doubling as a multiply (N=64800, same GB300: 7.617 against 7.653 ms)
 constexpr bool kShiftFma = LDPC_PP2_SHIFT_FMA != 0;
+// position indicators of the delta on the FMA pipe: more instructions for a
+// lighter ALU pipe, which lost (N=64800: 8.00 against 7.59 ms)
+constexpr bool kEqFma = LDPC_PP2_EQ_FMA != 0;
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -103,9 +109,15 @@ struct Delta {
   uint32_t Ao, Do, Io, SO;  // iteration k-2
   __device__ __forceinline__ Delta(const NewState& n, const SV& o)
       : An(n.An), Dn(hsub(n.Bn, n.An)), In(n.In), SN(n.Sn), Ao(o.A), Do(hsub(o.B, o.A)), Io(o.I), SO(o.S) {}
+  // [j = n~] as 1.0 / 0.0: a set instruction (ALU pipe), or sat(1 - |n~ - j|)
+  // with two FMA-pipe instructions (kEqFma), which the ALU-bound pass prefers
+  __device__ __forceinline__ static uint32_t ind(uint32_t I, int j) {
+    if constexpr (kEqFma) return hfma_sat(hab(hsub(I, h2c(j))), 0xBC00BC00u, 0x3C003C00u);
+    else return heq_one(I, h2c(j));
+  }
   __device__ __forceinline__ uint32_t next(int j, uint32_t two) {
-    const uint32_t Ln = hfma(Dn, heq_one(In, h2c(j)), An) ^ (SN & 0x80008000u);
-    const uint32_t Lo = hfma(Do, heq_one(Io, h2c(j)), Ao) ^ (SO & 0x80008000u);
+    const uint32_t Ln = hfma(Dn, ind(In, j), An) ^ (SN & 0x80008000u);
+    const uint32_t Lo = hfma(Do, ind(Io, j), Ao) ^ (SO & 0x80008000u);
     SN *= two;
     SO *= two;
     return hsub(Ln, Lo);

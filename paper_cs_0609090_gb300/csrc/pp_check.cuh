@@ -63,11 +63,14 @@ __device__ __forceinline__ NewState finish_state(uint32_t K1, uint32_t K2, uint3
   return n;
 }
 
+// Position j of a check; K1 = K2 = the saturated key before position 0.  At
+// j = 0 the second minimum stays the saturated key (every key is at most 1 and
+// min(ksat, max(ksat, key)) = ksat), so only the first is updated.
 __device__ __forceinline__ void key_step(uint32_t u, int j, uint32_t& K1, uint32_t& K2, uint32_t& NEG) {
   if (j == 0) NEG = u & 0x80008000u;
   else NEG = umad_hi(u & 0x80008000u, 1u << (32 - j), NEG);
   const uint32_t key = hfma_sat(hab(u), h2c_q11(16), h2c_q11(j));
-  K2 = hmin(K2, hmax(K1, key));
+  if (j != 0) K2 = hmin(K2, hmax(K1, key));
   K1 = hmin(K1, key);
 }
 
