@@ -726,20 +726,33 @@ def compare_forms(ldpc, code, w, llr, F, main_form, flush, stream, dev, main_ms)
     return out
 
 
-def fer_point(ldpc, code, w, llr, F, form, stream, dev):
-    """Frame error rate of the benchmarked decoder at the workload's Eb/N0 with
-    early stop on: the decisions of every frame against its transmitted codeword
-    (random codewords of the code, BPSK over AWGN), Wilson 95 % interval."""
+# Eb/N0 points (dB) of the FER curve the line carries, per workload: the
+# workload's own channel point first, then the code's waterfall region.
+FER_POINTS = {"irr_n64800": [1.0, 1.25, 1.5, 1.75, 2.0], "qc_n7493": [2.5, 2.75, 3.0],
+              "reg36_n1008": [2.0, 2.5, 3.0]}
+
+
+def fer_point(ldpc, code, w, llr, F, form, stream, dev, min_errors=100, max_frames=1 << 15):
+    """Frame error rates of the benchmarked decoder (early stop on) at the
+    stated Eb/N0 points: random codewords of the code (a pool from its encoder),
+    BPSK over AWGN generated on the device, the int8 channel quantization of the
+    workload; each point runs until min_errors frame errors or max_frames
+    frames, with a Wilson 95 % interval."""
     import torch
-    from paper_cs_0609090_gb300.fer import wilson
+    from paper_cs_0609090_gb300 import fer
     params = ldpc.make_params(form=form, **dict(w.params, early_stop=1))
-    _, bits, iters, ok = time_decode(ldpc, code, params, llr, F, torch.empty(1, device=dev), stream, dev, 1, 0)
-    dec = ldpc.unpack_bits(bits.cpu().numpy(), w.code.n_vars)
-    errors = int(np.any(dec != w.codewords, axis=1).sum())
-    return {"ebn0_db": w.ebn0_db, "frames": F, "errors": errors, "fer": errors / F, "wilson95": wilson(errors, F),
-            "mean_iters": float(iters.double().mean().item()), "max_iter": w.params["max_iter"],
-            "syndrome_ok": float(ok.double().mean().item()), "early_stop": 1,
-            "note": "one batch; the FER curves with >= 100 errors per point are in profiles/"}
+    pool = fer.CodewordPool(w.code, 256, seed=12345, device=dev)
+    run = fer.int8_decoder(code, params, w.delta, w.qc, F, dev)
+    rate = (w.code.n_vars - w.code.n_checks) / w.code.n_vars
+    pts = []
+    for eb in FER_POINTS.get(w.name, [w.ebn0_db]):
+        r = fer.run_point(run, w.code.n_vars, rate, eb, pool, min_errors=min_errors, max_frames=max_frames,
+                          batch=F, seed=99)
+        pts.append({k: r[k] for k in ("ebn0_db", "frames", "errors", "fer", "wilson95", "mean_iters")})
+    torch.cuda.synchronize()
+    return {"points": pts, "max_iter": w.params["max_iter"], "early_stop": 1, "form": form,
+            "codewords": "random, pool of 256 from the code's encoder (seed 12345); device AWGN, seed 99",
+            "stop": f">= {min_errors} frame errors or {max_frames} frames per point"}
 
 
 def main():
