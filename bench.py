@@ -728,7 +728,7 @@ def compare_forms(ldpc, code, w, llr, F, main_form, flush, stream, dev, main_ms)
 
 # Eb/N0 points (dB) of the FER curve the line carries, per workload: the
 # workload's own channel point first, then the code's waterfall region.
-FER_POINTS = {"irr_n64800": [1.0, 1.25, 1.5, 1.75, 2.0], "qc_n7493": [2.5, 2.75, 3.0],
+FER_POINTS = {"irr_n64800": [1.0, 1.5, 2.0, 2.5, 3.0], "qc_n7493": [2.5, 2.75, 3.0],
               "reg36_n1008": [2.0, 2.5, 3.0]}
 
 
