@@ -523,8 +523,8 @@ def run_multi(args, world, rank, local):
                        "ebn0_db": [w.ebn0_db for w in ws], "graph": "one CUDA graph replay per step",
                        "l2": "flushed between timed steps (256 MB write)",
                        "plan": {k: info[k] for k in ("threads", "team_threads", "cluster", "queue", "large",
-                                                    "grid", "smem_bytes", "job_is_cluster",
-                                                    "job_pairs_per_cta")},
+                                                    "overlap", "stream_warps", "grid", "smem_bytes",
+                                                    "job_is_cluster", "job_pairs_per_cta")},
                        "autotune_ms": tuned_ms},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(sum(w.q0.nbytes for w in ws)),
                     "d2h_bytes_per_step": int(sum(sum(t.numel() * t.element_size() for t in o[:3])

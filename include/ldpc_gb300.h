@@ -436,7 +436,11 @@ typedef struct {
  *   overlap       the codes on the streaming decoder: 0 (default) in sequence on
  *                 the caller's stream until ldpc_multi_autotune picks the faster
  *                 schedule; 1 always in sequence; 2 always overlapped on side
- *                 streams.  The autotuner keeps a schedule fixed by 1 or 2. */
+ *                 streams.  The autotuner keeps a schedule fixed by 1 or 2.
+ *   stream_warps  warps per CTA of the ping-pong decoder's row kernel for the
+ *                 streamed codes (four checks per warp, so 16, 32 or 64 checks
+ *                 per CTA): 4, 8 or 16; 0 (default) 8 until ldpc_multi_autotune
+ *                 times the three; a value set here is kept by the autotuner. */
 typedef struct {
   int32_t threads;
   int32_t team_threads;
@@ -444,6 +448,7 @@ typedef struct {
   int32_t queue;
   int32_t large;
   int32_t overlap;
+  int32_t stream_warps;
 } ldpc_multi_tuning;
 
 typedef struct ldpc_multi ldpc_multi;
@@ -477,7 +482,8 @@ LDPC_API ldpc_status ldpc_multi_decode(const ldpc_multi *plan, void *workspace, 
  * plan's own buffers, reps decodes each after one warm-up, with CUDA events on
  * `stream` (synchronising it), and keeps the fastest; then times that shape
  * with the streamed codes in sequence and overlapped (at least 5 decodes
- * each, back to back) and keeps the faster.  The decodes overwrite the
+ * each, back to back) and keeps the faster, and, when codes run on the
+ * ping-pong decoder, its row kernel at 4, 8 and 16 warps per CTA.  The decodes overwrite the
  * outputs (with the same values).  Not capturable.  chosen (host, nullable)
  * receives the kept shape, best_ms (host, nullable) its mean time. */
 LDPC_API ldpc_status ldpc_multi_autotune(ldpc_multi *plan, void *workspace, size_t ws_bytes, int32_t reps,

@@ -138,9 +138,10 @@ PingpongLayout pingpong_layout(int form, int N, int M, int ell_w, int F);
 // device (once per device, outside stream capture).
 cudaError_t pingpong_prepare();
 bool pingpong_int8_eligible(int N, int M, int ell_w, int max_row_deg, int max_col_deg, int qm, int form, int F);
+// warps: warps per block of the row kernel (4, 8 or 16; four checks per warp).
 cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, const PingpongLayout& L, void* ws,
                                  const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
-                                 int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st);
+                                 int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st, int warps = 8);
 
 // The two-scan algorithm of Section III with the frame state in device memory
 // (twoscan_stream.cu), any code size: per-edge Z_mn, and the check messages per

@@ -289,7 +289,7 @@ ldpc_status build(const std::vector<JobIn>& in, int form, const ldpc_multi_tunin
 }
 
 ldpc_multi_tuning normalize(const ldpc_multi_tuning* t) {
-  ldpc_multi_tuning s = {1024, 128, 0, 1, 1, 0};
+  ldpc_multi_tuning s = {1024, 128, 0, 1, 1, 0, 0};
   if (t != nullptr) {
     if (t->threads) s.threads = t->threads;
     if (t->team_threads) s.team_threads = t->team_threads;
@@ -297,6 +297,7 @@ ldpc_multi_tuning normalize(const ldpc_multi_tuning* t) {
     if (t->queue) s.queue = t->queue;
     if (t->large) s.large = t->large;
     s.overlap = t->overlap;
+    s.stream_warps = t->stream_warps;
   }
   return s;
 }
@@ -311,6 +312,8 @@ ldpc_status check_tuning(const ldpc_multi_tuning& s) {
   if (s.queue != 1 && s.queue != 2) return fail(LDPC_ERR_INVALID_ARG, "queue %d is not 1 or 2", s.queue);
   if (s.large != 1 && s.large != 2) return fail(LDPC_ERR_INVALID_ARG, "large %d is not 1 or 2", s.large);
   if (s.overlap < 0 || s.overlap > 2) return fail(LDPC_ERR_INVALID_ARG, "overlap %d is not 0, 1 or 2", s.overlap);
+  if (s.stream_warps != 0 && s.stream_warps != 4 && s.stream_warps != 8 && s.stream_warps != 16)
+    return fail(LDPC_ERR_INVALID_ARG, "stream_warps %d is not 0, 4, 8 or 16", s.stream_warps);
   return LDPC_OK;
 }
 
@@ -411,7 +414,8 @@ cudaError_t launch_plan(const ldpc_multi* p, void* ws, cudaStream_t st) {
     if (sj.pingpong)
       e = ldpc::pingpong_int8_decode(view(jb.code), r, p->form, sj.pp, static_cast<char*>(ws) + sj.offset, jb.llr,
                                      jb.n_frames, jb.params.max_iter, jb.params.early_stop, jb.hard_bits,
-                                     jb.iters_used, jb.syndrome_ok, jb.llr_out, ss);
+                                     jb.iters_used, jb.syndrome_ok, jb.llr_out, ss,
+                                     p->shape.stream_warps ? p->shape.stream_warps : 8);
     else
       e = ldpc::stream_int8_decode(view(jb.code), r, p->form, sj.layout, static_cast<char*>(ws) + sj.offset,
                                    jb.code->sm_count, jb.llr, jb.n_frames, jb.params.max_iter, jb.params.early_stop,
@@ -656,6 +660,27 @@ ldpc_status ldpc_multi_autotune(ldpc_multi* plan, void* workspace, size_t ws_byt
         plan->overlap = t_ovl < t_seq;
         best_t = plan->overlap ? t_ovl : t_seq;
       }
+    }
+    // warps per CTA of the ping-pong row kernel for the streamed codes: the
+    // workspace does not depend on it, so the plan is timed as it stands
+    bool any_pp = false;
+    for (const ldpc_multi::StreamJob& sj : plan->streamed) any_pp = any_pp || sj.pingpong;
+    if (s == LDPC_OK && result == LDPC_OK && any_pp && start.stream_warps == 0) {
+      const int n = reps > 5 ? reps : 5;
+      int best_w = 8;
+      float best_wt = -1.0f;
+      for (int w : {4, 8, 16}) {
+        plan->shape.stream_warps = w;
+        float ms = 0.0f;
+        const cudaError_t e = time_plan(n, &ms);
+        if (e != cudaSuccess) {
+          result = cuda_fail(e, "autotune stream_warps");
+          break;
+        }
+        if (best_wt < 0.0f || ms < best_wt) best_wt = ms, best_w = w;
+      }
+      plan->shape.stream_warps = best_w;
+      if (result == LDPC_OK) best_t = best_wt;
     }
   }
   cudaEventDestroy(e0);

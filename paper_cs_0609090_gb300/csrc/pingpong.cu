@@ -63,12 +63,12 @@ constexpr uint32_t kFull = 0xffffffffu;
 #define LDPC_PP2_UNROLL 4
 #endif
 
-constexpr int kWarps = 8;   // per block
+constexpr int kWarps = 8;   // per block (pp2_final; the row kernel's default)
+constexpr int kRowWarpsMax = 16;  // the row kernel takes 4, 8 or 16 warps per block
 constexpr int kRows = 4;    // checks per handle group (kRows x degree <= 32 lanes)
 constexpr int kTile = kWarps * kRows;
 constexpr int kStages = LDPC_PP2_STAGES;  // staged checks in flight + 1
 constexpr int kGroups = LDPC_PP2_GROUPS;  // handle groups per warp in the row kernel
-constexpr int kRowTile = kTile * kGroups;  // checks per row-kernel block
 constexpr int kUnroll = LDPC_PP2_UNROLL;   // unrolling of the staged check loop
 // sign-word doubling as a multiply (N=64800, same GB300: 7.617 against 7.653 ms)
 constexpr bool kShiftFma = LDPC_PP2_SHIFT_FMA != 0;
@@ -269,7 +269,7 @@ struct Stage {
   uint2 z[kStages][7][32];
   uint4 s[kStages][2][32];
 };
-constexpr size_t kStageBytes = sizeof(Stage) * kWarps;
+constexpr size_t kStageBytes = sizeof(Stage) * kRowWarpsMax;
 
 template <bool ES, int D>
 __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const uint32_t* hl, int lane, Stage& sg) {
@@ -309,14 +309,17 @@ __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const 
   return fail;
 }
 
-// Row kernel of iteration k: block (bx, chunk) takes kRowTile checks of the
-// degree-sorted order for the chunk's 64 pairs (warp w: checks bx kRowTile + w
-// kRows kGroups ..., lane l: pairs chunk 64 + 2 l, + 1).
+// Row kernel of iteration k: block (bx, chunk) of nw warps takes nw kRows
+// kGroups checks of the degree-sorted order for the chunk's 64 pairs (warp w:
+// checks (bx nw + w) kRows kGroups ..., lane l: pairs chunk 64 + 2 l, + 1).
 template <int FORM, bool ES>
 // CTAs per SM (registers 65536 / (256 x this)), measured on the N=64800 code:
 // Section V with staged inputs 4 (7.83 ms, 52 bytes of spills, against 8.16 ms
 // at 3 without spills; 5 spills 436 bytes), per edge 4 (11.99 against 12.38)
-__global__ void __launch_bounds__(kWarps * 32, FORM == 1 ? LDPC_PP2_MINB1 : 4) pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
+// Blocks of 4, 8 or 16 warps (blockDim.x / 32 = nw); the bound keeps the
+// registers of 256 threads x MINB1 CTAs for every block size.
+__global__ void __launch_bounds__(kRowWarpsMax * 32, FORM == 1 ? LDPC_PP2_MINB1 * kWarps / kRowWarpsMax : 4 * kWarps / kRowWarpsMax)
+pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.y * 64 + 2 * lane;
   const int FP = s.FP;
@@ -355,7 +358,8 @@ __global__ void __launch_bounds__(kWarps * 32, FORM == 1 ? LDPC_PP2_MINB1 : 4) p
   // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
   x.ksat = hfma(ints_to_h2(ir.qm, ir.qm), h2c_q11(16), h2c_q11(15));
   x.two = s.two;
-  const int m0 = blockIdx.x * kRowTile + warp * kRows * kGroups;
+  const int nw = blockDim.x >> 5;
+  const int m0 = (blockIdx.x * nw + warp) * kRows * kGroups;
   const int nr = min(kRows * kGroups, c.M - m0);
   if (nr <= 0) return;
   uint32_t fail = 0;
@@ -577,14 +581,15 @@ __global__ void __launch_bounds__(256) pp2_output(const DevCode c, PP2 s, int K,
 }
 
 template <int FORM, bool ES>
-cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, const int8_t* llr, int K, uint8_t* bits,
+cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, int warps, const int8_t* llr, int K, uint8_t* bits,
                     int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
   const dim3 tgrid((unsigned)((c.N + 63) / 64), (unsigned)(s.FP / 32));
   const dim3 rgrid((unsigned)((c.M + kTile - 1) / kTile), (unsigned)(s.FP / 64));
-  const dim3 rgrid_rows((unsigned)((c.M + kRowTile - 1) / kRowTile), (unsigned)(s.FP / 64));
+  const int row_tile = warps * kRows * kGroups;
+  const dim3 rgrid_rows((unsigned)((c.M + row_tile - 1) / row_tile), (unsigned)(s.FP / 64));
   pp2_init<ES><<<tgrid, 256, 0, st>>>(c, llr, s, K);
-  const size_t smem = FORM == 1 && LDPC_PP2_STAGED ? kStageBytes : 0;
-  for (int k = 1; k <= K; ++k) pp2_rows<FORM, ES><<<rgrid_rows, kWarps * 32, smem, st>>>(c, r, s, k);
+  const size_t smem = FORM == 1 && LDPC_PP2_STAGED ? sizeof(Stage) * warps : 0;
+  for (int k = 1; k <= K; ++k) pp2_rows<FORM, ES><<<rgrid_rows, warps * 32, smem, st>>>(c, r, s, k);
   pp2_final<ES><<<rgrid, kWarps * 32, 0, st>>>(c, s, K);
   pp2_output<<<tgrid, 256, 0, st>>>(c, s, K, bits, iters, ok, zout);
   return cudaGetLastError();
@@ -628,7 +633,8 @@ bool pingpong_int8_eligible(int N, int M, int ell_w, int max_row_deg, int max_co
 
 cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, const PingpongLayout& L, void* ws,
                                  const int8_t* llr, int32_t F, int32_t max_iter, int32_t early_stop, uint8_t* bits,
-                                 int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
+                                 int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st, int warps) {
+  if (warps != 4 && warps != 8 && warps != 16) return cudaErrorInvalidValue;
   char* b = static_cast<char*>(ws);
   PP2 s;
   s.zb = reinterpret_cast<uint32_t*>(b + L.zb);
@@ -645,10 +651,10 @@ cudaError_t pingpong_int8_decode(const DevCode& c, const IntRule& r, int form, c
   // L^(0) = L^(-1) = 0: Section V state all zero, per-edge bytes L + 128 = 0x80
   cudaError_t e = cudaMemsetAsync(b + L.st, form == 1 ? 0 : 0x80, L.act - L.st, st);
   if (e != cudaSuccess) return e;
-  if (form == 1) return early_stop ? pp2_run<1, true>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
-                                   : pp2_run<1, false>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
-  return early_stop ? pp2_run<0, true>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
-                    : pp2_run<0, false>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
+  if (form == 1) return early_stop ? pp2_run<1, true>(c, r, s, warps, llr, max_iter, bits, iters, ok, zout, st)
+                                   : pp2_run<1, false>(c, r, s, warps, llr, max_iter, bits, iters, ok, zout, st);
+  return early_stop ? pp2_run<0, true>(c, r, s, warps, llr, max_iter, bits, iters, ok, zout, st)
+                    : pp2_run<0, false>(c, r, s, warps, llr, max_iter, bits, iters, ok, zout, st);
 }
 
 }  // namespace ldpc

@@ -78,7 +78,8 @@ class ldpc_multi_job(ctypes.Structure):
 
 class ldpc_multi_tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("team_threads", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("queue", ctypes.c_int32), ("large", ctypes.c_int32), ("overlap", ctypes.c_int32)]
+                ("queue", ctypes.c_int32), ("large", ctypes.c_int32), ("overlap", ctypes.c_int32),
+                ("stream_warps", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -358,7 +359,8 @@ def ldpc_multi_info(plan: int, n_jobs: int) -> dict:
     _check(_lib.ldpc_multi_info(_P(plan), ctypes.byref(t), ctypes.byref(grid), ctypes.byref(cluster),
                                 ctypes.byref(smem), is_cl, pairs), "ldpc_multi_info")
     return {"threads": t.threads, "team_threads": t.team_threads, "cluster": cluster.value, "queue": t.queue,
-            "large": t.large, "overlap": t.overlap, "grid": grid.value, "smem_bytes": smem.value,
+            "large": t.large, "overlap": t.overlap, "stream_warps": t.stream_warps, "grid": grid.value,
+            "smem_bytes": smem.value,
             "job_is_cluster": list(is_cl),
             "job_pairs_per_cta": list(pairs)}
 

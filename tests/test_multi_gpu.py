@@ -183,6 +183,30 @@ def test_multi_batch_autotune(L, overlap):
     _multi_check(L, mb, ws, _multi_oracle(ws, form))
 
 
+@pytest.mark.parametrize("form", ["ss_1bit", "ss_fixed"])
+@pytest.mark.parametrize("warps", [4, 16])
+def test_multi_batch_stream_warps(L, form, warps):
+    """The ping-pong row kernel of the streamed staircase codes at 4 and 16
+    warps per CTA (16 and 64 checks per CTA) decodes exactly as the oracle;
+    a value fixed by the caller survives the autotuner, 0 lets it choose (when
+    its plan streams codes at all)."""
+    ws = I.make_multi_workload(frames=[4, 3, 2, 5, 3, 9, 7, 5], frame_seed=12)
+    mb, _, _ = _batch(L, ws, form, L.ldpc_multi_tuning(0, 0, 0, 0, 0, 2, warps))
+    assert mb.info()["stream_warps"] == warps
+    mb.decode()
+    _multi_check(L, mb, ws, _multi_oracle(ws, form))
+    shape, _ = mb.autotune(reps=1)
+    assert shape.stream_warps == warps
+    mb2, _, _ = _batch(L, ws, form, None)
+    shape, _ = mb2.autotune(reps=1)
+    # a plan that keeps every code inside the persistent launch (clusters) has
+    # no ping-pong row kernel to tune
+    streamed = 2 in mb2.info()["job_is_cluster"]
+    assert shape.stream_warps in ((4, 8, 16) if streamed else (0,))
+    mb2.decode()
+    _multi_check(L, mb2, ws, _multi_oracle(ws, form))
+
+
 def test_multi_rejects_bad_batches(L):
     import torch
     ws = I.make_multi_workload(frames=[3, 3, 0, 0, 0, 0, 0, 0], codes=[0, 1])
@@ -200,4 +224,8 @@ def test_multi_rejects_bad_batches(L):
     assert e.value.status == L.LDPC_ERR_INVALID_ARG
     with pytest.raises(L.LdpcError) as e:       # a shape outside the documented ranges
         L.MultiBatch(codes, llrs, [L.make_params(**w.params) for w in ws], tuning=L.ldpc_multi_tuning(300, 0, 0, 0))
+    assert e.value.status == L.LDPC_ERR_INVALID_ARG
+    with pytest.raises(L.LdpcError) as e:       # stream_warps outside 0, 4, 8, 16
+        L.MultiBatch(codes, llrs, [L.make_params(**w.params) for w in ws],
+                     tuning=L.ldpc_multi_tuning(0, 0, 0, 0, 0, 0, 6))
     assert e.value.status == L.LDPC_ERR_INVALID_ARG
