@@ -44,6 +44,15 @@ namespace {
 #endif
 
 constexpr uint32_t kFull = 0xffffffffu;
+// CTAs per SM of the per-edge row kernel (registers 65536 / (256 x this)): its
+// staged body needs 80 registers; at 64 it spills 580 bytes (N=64800 per-edge
+// decode: 11.05 ms staged at 3, 14.10 ms staged at 4, 11.36 ms unstaged at 4)
+#ifndef LDPC_PP2_MINB0
+#define LDPC_PP2_MINB0 3
+#endif
+#ifndef LDPC_PP2_STAGED_PE
+#define LDPC_PP2_STAGED_PE 1
+#endif
 #ifndef LDPC_PP2_STAGES
 #define LDPC_PP2_STAGES 2
 #endif
@@ -65,6 +74,10 @@ constexpr uint32_t kFull = 0xffffffffu;
 
 constexpr int kWarps = 8;   // per block (pp2_final; the row kernel's default)
 constexpr int kRowWarpsMax = 16;  // the row kernel takes 4, 8 or 16 warps per block
+// registers per thread of the row kernel: those of MINB CTAs of 256 threads per
+// SM, rounded down to the allocation unit of 8
+constexpr int kRegs1 = (65536 / (LDPC_PP2_MINB1 * 256)) & ~7;
+constexpr int kRegs0 = (65536 / (LDPC_PP2_MINB0 * 256)) & ~7;
 constexpr int kRows = 4;    // checks per handle group (kRows x degree <= 32 lanes)
 constexpr int kTile = kWarps * kRows;
 constexpr int kStages = LDPC_PP2_STAGES;  // staged checks in flight + 1
@@ -130,6 +143,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
                "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
                "l"(gmem) : "memory");
@@ -186,6 +203,51 @@ __device__ __forceinline__ uint32_t check2_sv(const RowArgs& x, int m, int d, co
   return pa | (pb << 2);
 }
 
+// The per-edge check from its inputs: posteriors wa / wb of the lane's two
+// pairs, the per-edge byte pairs of iterations k-1 (l1) and k-2 (l2) at each
+// position.  Adds L^(k) - L^(k-2) at the handles h[j] and overwrites the k-2
+// slots with L^(k).  Returns the decision parities as check2.
+template <bool ES, int D>
+__device__ __forceinline__ uint32_t check2_pe(const RowArgs& x, int m, int d, const uint32_t* h, const uint32_t* wa,
+                                              const uint32_t* wb, const uint32_t* l1, const uint32_t* l2) {
+  constexpr int NJ = D > 0 ? D : 8;
+  uint32_t pa = 0, pb = 0;
+  uint32_t K1a = x.ksat, K2a = x.ksat, NEGa = 0, Ya = 0, K1b = x.ksat, K2b = x.ksat, NEGb = 0, Yb = 0;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      key_step(hsub(wa[j], pe_to_h2(l1[j] & 0xffffu)), j, K1a, K2a, NEGa);
+      key_step(hsub(wb[j], pe_to_h2(l1[j] >> 16)), j, K1b, K2b, NEGb);
+      if (ES) {
+        Ya ^= dec_bits(wa[j]);
+        Yb ^= dec_bits(wb[j]);
+      }
+    }
+  }
+  const int dd = D > 0 ? D : d;
+  const NewState na = finish_state(K1a, K2a, NEGa, dd, x.rule), nb = finish_state(K1b, K2b, NEGb, dd, x.rule);
+  const uint32_t Dna = hsub(na.Bn, na.An), Dnb = hsub(nb.Bn, nb.An);
+  uint32_t SNa = na.Sn, SNb = nb.Sn;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      const uint32_t La = hfma(Dna, heq_one(na.In, h2c(j)), na.An) ^ (SNa & 0x80008000u);
+      const uint32_t Lb = hfma(Dnb, heq_one(nb.In, h2c(j)), nb.An) ^ (SNb & 0x80008000u);
+      SNa += SNa;
+      SNb += SNb;
+      const uint32_t da = ES ? hsub(La, pe_to_h2(l2[j] & 0xffffu)) & x.amA : hsub(La, pe_to_h2(l2[j] & 0xffffu));
+      const uint32_t db = ES ? hsub(Lb, pe_to_h2(l2[j] >> 16)) & x.amB : hsub(Lb, pe_to_h2(l2[j] >> 16));
+      if (!ES || (x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
+      __stcg(reinterpret_cast<uint32_t*>(x.S2 + (size_t)(j * x.M + m) * x.FP * 2), h2_to_pe(La) | (h2_to_pe(Lb) << 16));
+    }
+  }
+  if (ES) {
+    pa = ((Ya >> 15) & 1u) | ((Ya >> 30) & 2u);
+    pb = ((Yb >> 15) & 1u) | ((Yb >> 30) & 2u);
+  }
+  return pa | (pb << 2);
+}
+
 // One check m of degree d (D > 0: exactly D) for the lane's two pairs, handles
 // h[j] (variable x FP).  Returns the decision parities of x^(k-1) of both pairs
 // (bits 0-1 first pair, 2-3 second).
@@ -201,7 +263,6 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
       wb[j] = v.y;
     }
   }
-  uint32_t pa = 0, pb = 0;
   if constexpr (FORM == 1) {
     const size_t so = (size_t)m * x.FP * 8;
     const uint4 s1 = __ldcg(reinterpret_cast<const uint4*>(x.S1 + so));
@@ -218,41 +279,8 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
         l2[j] = __ldcg(reinterpret_cast<const uint32_t*>(x.S2 + so));
       }
     }
-    uint32_t K1a = x.ksat, K2a = x.ksat, NEGa = 0, Ya = 0, K1b = x.ksat, K2b = x.ksat, NEGb = 0, Yb = 0;
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      if (D > 0 || j < d) {
-        key_step(hsub(wa[j], pe_to_h2(l1[j] & 0xffffu)), j, K1a, K2a, NEGa);
-        key_step(hsub(wb[j], pe_to_h2(l1[j] >> 16)), j, K1b, K2b, NEGb);
-        if (ES) {
-          Ya ^= dec_bits(wa[j]);
-          Yb ^= dec_bits(wb[j]);
-        }
-      }
-    }
-    const int dd = D > 0 ? D : d;
-    const NewState na = finish_state(K1a, K2a, NEGa, dd, x.rule), nb = finish_state(K1b, K2b, NEGb, dd, x.rule);
-    const uint32_t Dna = hsub(na.Bn, na.An), Dnb = hsub(nb.Bn, nb.An);
-    uint32_t SNa = na.Sn, SNb = nb.Sn;
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      if (D > 0 || j < d) {
-        const uint32_t La = hfma(Dna, heq_one(na.In, h2c(j)), na.An) ^ (SNa & 0x80008000u);
-        const uint32_t Lb = hfma(Dnb, heq_one(nb.In, h2c(j)), nb.An) ^ (SNb & 0x80008000u);
-        SNa += SNa;
-        SNb += SNb;
-        const uint32_t da = ES ? hsub(La, pe_to_h2(l2[j] & 0xffffu)) & x.amA : hsub(La, pe_to_h2(l2[j] & 0xffffu));
-        const uint32_t db = ES ? hsub(Lb, pe_to_h2(l2[j] >> 16)) & x.amB : hsub(Lb, pe_to_h2(l2[j] >> 16));
-        if (!ES || (x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
-        __stcg(reinterpret_cast<uint32_t*>(x.S2 + (size_t)(j * x.M + m) * x.FP * 2), h2_to_pe(La) | (h2_to_pe(Lb) << 16));
-      }
-    }
-    if (ES) {
-      pa = ((Ya >> 15) & 1u) | ((Ya >> 30) & 2u);
-      pb = ((Yb >> 15) & 1u) | ((Yb >> 30) & 2u);
-    }
+    return check2_pe<ES, D>(x, m, d, h, wa, wb, l1, l2);
   }
-  return pa | (pb << 2);
 }
 
 // Per-warp staging of the Section V checks of uniform degree D <= 7: the
@@ -265,22 +293,42 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
 // the inputs read straight from global memory; three stages 8.87 ms, two
 // groups 8.35 ms, four groups 13.1 ms; the loop unrolled 1 or 2 times instead
 // of 4: +1.6 % / +1.3 %.
-struct Stage {
+template <int FORM>
+struct Stage;
+template <>
+struct Stage<1> {  // posterior pairs and both 16-byte state words per lane
   uint2 z[kStages][7][32];
   uint4 s[kStages][2][32];
 };
-constexpr size_t kStageBytes = sizeof(Stage) * kRowWarpsMax;
+template <>
+struct Stage<0> {  // posterior pairs and the k-1 / k-2 message words of each position
+  uint2 z[kStages][7][32];
+  uint32_t l1[kStages][7][32];
+  uint32_t l2[kStages][7][32];
+};
+// per-edge staging: 57,344 bytes per 8-warp CTA, so that 4 CTAs with their
+// 1 KB reservations fill the SM's 233,472 bytes exactly
 
-template <bool ES, int D>
-__device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const uint32_t* hl, int lane, Stage& sg) {
+template <int FORM, bool ES, int D>
+__device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const uint32_t* hl, int lane,
+                                                Stage<FORM>& sg) {
   constexpr int T = kRows * kGroups;
   const auto issue = [&](int t) {
     const int b = t % kStages, g = t / kRows, r = t - g * kRows;
 #pragma unroll
     for (int j = 0; j < D; ++j) cp_async8(&sg.z[b][j][lane], x.Zr + __shfl_sync(kFull, hl[g], r * D + j));
-    const size_t so = (size_t)(m0 + t) * x.FP * 8;
-    cp_async16(&sg.s[b][0][lane], x.S1 + so);
-    cp_async16(&sg.s[b][1][lane], x.S2 + so);
+    if constexpr (FORM == 1) {
+      const size_t so = (size_t)(m0 + t) * x.FP * 8;
+      cp_async16(&sg.s[b][0][lane], x.S1 + so);
+      cp_async16(&sg.s[b][1][lane], x.S2 + so);
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const size_t so = (size_t)(j * x.M + m0 + t) * x.FP * 2;
+        cp_async4(&sg.l1[b][j][lane], x.S1 + so);
+        cp_async4(&sg.l2[b][j][lane], x.S2 + so);
+      }
+    }
   };
   uint32_t fail = 0;
 #pragma unroll
@@ -304,7 +352,17 @@ __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const 
       wa[j] = v.x;
       wb[j] = v.y;
     }
-    fail |= check2_sv<ES, D>(x, m0 + t, D, h, wa, wb, sg.s[b][0][lane], sg.s[b][1][lane]);
+    if constexpr (FORM == 1) {
+      fail |= check2_sv<ES, D>(x, m0 + t, D, h, wa, wb, sg.s[b][0][lane], sg.s[b][1][lane]);
+    } else {
+      uint32_t l1[D], l2[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        l1[j] = sg.l1[b][j][lane];
+        l2[j] = sg.l2[b][j][lane];
+      }
+      fail |= check2_pe<ES, D>(x, m0 + t, D, h, wa, wb, l1, l2);
+    }
   }
   return fail;
 }
@@ -313,12 +371,12 @@ __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const 
 // kGroups checks of the degree-sorted order for the chunk's 64 pairs (warp w:
 // checks (bx nw + w) kRows kGroups ..., lane l: pairs chunk 64 + 2 l, + 1).
 template <int FORM, bool ES>
-// CTAs per SM (registers 65536 / (256 x this)), measured on the N=64800 code:
-// Section V with staged inputs 4 (7.83 ms, 52 bytes of spills, against 8.16 ms
-// at 3 without spills; 5 spills 436 bytes), per edge 4 (11.99 against 12.38)
+// CTAs per SM (registers 65536 / (256 x LDPC_PP2_MINB1 or _MINB0)), measured on
+// the N=64800 code: Section V with staged inputs 4 (7.83 ms, 52 bytes of spills,
+// against 8.16 ms at 3 without spills; 5 spills 436 bytes); per edge 3.
 // Blocks of 4, 8 or 16 warps (blockDim.x / 32 = nw); the bound keeps the
 // registers of 256 threads x MINB1 CTAs for every block size.
-__global__ void __launch_bounds__(kRowWarpsMax * 32, FORM == 1 ? LDPC_PP2_MINB1 * kWarps / kRowWarpsMax : 4 * kWarps / kRowWarpsMax)
+__global__ void __launch_bounds__(kRowWarpsMax * 32) __maxnreg__(FORM == 1 ? kRegs1 : kRegs0)
 pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.y * 64 + 2 * lane;
@@ -377,10 +435,10 @@ pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
       }
     }
 #if LDPC_PP2_STAGED
-    if constexpr (FORM == 1) {
+    if constexpr (FORM == 1 || LDPC_PP2_STAGED_PE) {
       extern __shared__ __align__(16) unsigned char pp2_smem[];
-      Stage& sg = reinterpret_cast<Stage*>(pp2_smem)[warp];
-      fail = d0 == 6 ? rows_staged<ES, 6>(x, m0, hl, lane, sg) : rows_staged<ES, 7>(x, m0, hl, lane, sg);
+      Stage<FORM>& sg = reinterpret_cast<Stage<FORM>*>(pp2_smem)[warp];
+      fail = d0 == 6 ? rows_staged<FORM, ES, 6>(x, m0, hl, lane, sg) : rows_staged<FORM, ES, 7>(x, m0, hl, lane, sg);
     } else
 #endif
 #pragma unroll
@@ -588,7 +646,7 @@ cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, int warps,
   const int row_tile = warps * kRows * kGroups;
   const dim3 rgrid_rows((unsigned)((c.M + row_tile - 1) / row_tile), (unsigned)(s.FP / 64));
   pp2_init<ES><<<tgrid, 256, 0, st>>>(c, llr, s, K);
-  const size_t smem = FORM == 1 && LDPC_PP2_STAGED ? sizeof(Stage) * warps : 0;
+  const size_t smem = LDPC_PP2_STAGED && (FORM == 1 || LDPC_PP2_STAGED_PE) ? sizeof(Stage<FORM>) * warps : 0;
   for (int k = 1; k <= K; ++k) pp2_rows<FORM, ES><<<rgrid_rows, warps * 32, smem, st>>>(c, r, s, k);
   pp2_final<ES><<<rgrid, kWarps * 32, 0, st>>>(c, s, K);
   pp2_output<<<tgrid, 256, 0, st>>>(c, s, K, bits, iters, ok, zout);
@@ -598,10 +656,16 @@ cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, int warps,
 }  // namespace
 
 cudaError_t pingpong_prepare() {
-  // the staged Section V row kernels take kStageBytes of dynamic shared memory;
+  // the staged row kernels take up to kRowWarpsMax Stage<FORM> of dynamic shared memory;
   // set on the current device outside any stream capture (code creation)
   for (auto f : {pp2_rows<1, false>, pp2_rows<1, true>}) {
-    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(Stage<1>) * kRowWarpsMax));
+    if (e != cudaSuccess) return e;
+  }
+  for (auto f : {pp2_rows<0, false>, pp2_rows<0, true>}) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(Stage<0>) * kRowWarpsMax));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
