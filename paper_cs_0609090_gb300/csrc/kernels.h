@@ -150,6 +150,7 @@ struct TwoScanLayout {
   int lanes = 0;   // frame pairs, padded to 64
   bool c8 = false; // compressed state in 8 bytes per pair (check degree <= 8), else 16
   int ub = 0;
+  int dvmax = 16;  // largest column degree of the code (set by the caller; <= 16)
   size_t zmn = 0, lmn = 0, st = 0, q0 = 0, zp = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
 };
 TwoScanLayout twoscan_layout(int form2, int N, int M, int ell_w, int F);

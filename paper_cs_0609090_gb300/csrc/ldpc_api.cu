@@ -268,6 +268,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
                                       n_frames)) {
       ch->kind = Choice::STREAM_TWOSCAN;
       ch->twoscan = ldpc::twoscan_layout(form2, c->N, c->M, c->ell_w, n_frames);
+      ch->twoscan.dvmax = c->max_col_deg;
       ch->ws = ch->twoscan.total;
       return LDPC_OK;
     }

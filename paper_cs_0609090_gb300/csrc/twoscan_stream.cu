@@ -24,6 +24,7 @@
 // (variables: Z_n = q0 + sum_m L_mn, Z_mn = Z_n - L_mn).  The decode starts with
 // a vertical scan over L = 0 (Z_mn = q0) and ends with the syndrome of x^(K).
 #include <algorithm>
+#include <type_traits>
 
 #include "h2_body.cuh"
 #include "kernels.h"
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kWarps * 32) ts_horizontal(const DevCode c, co
 // posterior when `post` (the last iteration, or every one with early stop) for
 // the frames that continue; with early stop the first block of a chunk stops
 // the frames whose x^(k-1) satisfied H.
-template <int FORM2, bool C8, bool ES>
+template <int FORM2, bool C8, bool ES, int DVM>
 __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s, int k, int post) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.y * 64 + 2 * lane;
@@ -198,16 +199,41 @@ __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s
   const uint32_t selA = half_mask(aA), selB = half_mask(aB);
   const int n0 = (blockIdx.x * kWarps + warp) * kCols;
   const int n1 = min(n0 + kCols, c.N);
+  if (n0 >= n1) return;
+  // the edge slots (and, compressed, the check / position words) of the warp's
+  // variables, one per lane, loaded together: at most kCols DVM <= 64 edges, so
+  // two words per lane; each variable then reads them with shuffles instead of
+  // a dependent load ahead of its message gathers
+  constexpr int kEdgeWords = (kCols * DVM + 31) / 32;
+  const int ew0 = __ldg(c.cptr + n0), ewn = __ldg(c.cptr + n1) - ew0;
+  uint32_t slw[kEdgeWords], cjw[kEdgeWords];
+#pragma unroll
+  for (int q = 0; q < kEdgeWords; ++q) {
+    const int e = q * 32 + lane;
+    slw[q] = e < ewn ? (uint32_t)__ldg(c.cslot + ew0 + e) : 0u;
+    cjw[q] = 0u;
+    if constexpr (FORM2 == 1) cjw[q] = e < ewn ? __ldg(c.ccj + ew0 + e) : 0u;
+  }
+  const auto pick = [&](const uint32_t* w, int e) {
+    uint32_t v = __shfl_sync(kFull, w[0], e & 31);
+#pragma unroll
+    for (int q = 1; q < kEdgeWords; ++q) {
+      const uint32_t u = __shfl_sync(kFull, w[q], e & 31);
+      if ((e >> 5) == q) v = u;
+    }
+    return v;
+  };
   for (int n = n0; n < n1; ++n) {
     const int e0 = __ldg(c.cptr + n), dv = __ldg(c.cptr + n + 1) - e0;
     const uint32_t q = __ldcg(reinterpret_cast<const uint32_t*>(s.q0 + (size_t)n * FP + p));
     uint32_t za = by_to_h2(q), zb = by_to_h2(q >> 16);
-    uint32_t La[kDvMax], Lb[kDvMax];
-    uint32_t sl[kDvMax];
+    uint32_t La[DVM], Lb[DVM];
+    uint32_t sl[DVM];
 #pragma unroll
-    for (int a = 0; a < kDvMax; ++a) {
+    for (int a = 0; a < DVM; ++a) {
+      // warp-uniform bound: every lane takes part in the shuffles
       if (a < dv) {
-        sl[a] = (uint32_t)__ldg(c.cslot + e0 + a);
+        sl[a] = pick(slw, e0 - ew0 + a);
         if (k == 0) {
           La[a] = 0u;
           Lb[a] = 0u;
@@ -216,7 +242,7 @@ __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s
           La[a] = by_to_h2(l);
           Lb[a] = by_to_h2(l >> 16);
         } else {
-          const uint32_t cj = __ldg(c.ccj + e0 + a);  // internal check | position << 24
+          const uint32_t cj = pick(cjw, e0 - ew0 + a);  // internal check | position << 24
           const uint32_t m = cj & 0xffffffu, j = cj >> 24;
           SV oa, ob;
           if constexpr (C8) {
@@ -248,7 +274,7 @@ __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s
       __stcg(Z, v);
     }
 #pragma unroll
-    for (int a = 0; a < kDvMax; ++a) {
+    for (int a = 0; a < DVM; ++a) {
       if (a < dv) {
         const uint32_t ba = h2_to_by_sat(hsub(za, La[a])), bb = h2_to_by_sat(hsub(zb, Lb[a]));
         __stcg(reinterpret_cast<uint32_t*>(s.zmn + (size_t)sl[a] * FP + p), ba | (bb << 16));
@@ -369,17 +395,17 @@ __global__ void __launch_bounds__(256) ts_output(const DevCode c, TS s, int K, u
   }
 }
 
-template <int FORM2, bool C8, bool ES>
+template <int FORM2, bool C8, bool ES, int DVM>
 cudaError_t ts_run(const DevCode& c, const IntRule& r, const TS& s, const int8_t* llr, int K, uint8_t* bits,
                    int32_t* iters, uint8_t* ok, int16_t* zout, cudaStream_t st) {
   const dim3 tgrid((unsigned)((c.N + 63) / 64), (unsigned)(s.FP / 32));
   const dim3 hgrid((unsigned)((c.M + kWarps * kRows - 1) / (kWarps * kRows)), (unsigned)(s.FP / 64));
   const dim3 vgrid((unsigned)((c.N + kWarps * kCols - 1) / (kWarps * kCols)), (unsigned)(s.FP / 64));
   ts_init<ES><<<tgrid, 256, 0, st>>>(c, llr, s, K);
-  ts_vertical<FORM2, C8, ES><<<vgrid, kWarps * 32, 0, st>>>(c, s, 0, (ES || K == 0) ? 1 : 0);
+  ts_vertical<FORM2, C8, ES, DVM><<<vgrid, kWarps * 32, 0, st>>>(c, s, 0, (ES || K == 0) ? 1 : 0);
   for (int k = 1; k <= K; ++k) {
     ts_horizontal<FORM2, C8, ES><<<hgrid, kWarps * 32, 0, st>>>(c, r, s, k);
-    ts_vertical<FORM2, C8, ES><<<vgrid, kWarps * 32, 0, st>>>(c, s, k, (ES || k == K) ? 1 : 0);
+    ts_vertical<FORM2, C8, ES, DVM><<<vgrid, kWarps * 32, 0, st>>>(c, s, k, (ES || k == K) ? 1 : 0);
   }
   ts_final<ES><<<hgrid, kWarps * 32, 0, st>>>(c, s, K);
   ts_output<<<tgrid, 256, 0, st>>>(c, s, K, bits, iters, ok, zout);
@@ -433,12 +459,18 @@ cudaError_t twoscan_stream_decode(const DevCode& c, const IntRule& r, int form2,
   s.FP = L.lanes;
   s.ub = L.ub;
   const bool es = early_stop != 0;
-  if (form2 == 0) return es ? ts_run<0, true, true>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
-                            : ts_run<0, true, false>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
-  if (L.c8) return es ? ts_run<1, true, true>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
-                      : ts_run<1, true, false>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
-  return es ? ts_run<1, false, true>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
-            : ts_run<1, false, false>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
+  // the vertical kernel keeps a column's messages in arrays of 8 entries when
+  // every column has degree <= 8 (fewer registers, more warps), else 16
+  const auto run = [&](auto dvm) {
+    constexpr int DVM = decltype(dvm)::value;
+    if (form2 == 0) return es ? ts_run<0, true, true, DVM>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
+                              : ts_run<0, true, false, DVM>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
+    if (L.c8) return es ? ts_run<1, true, true, DVM>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
+                        : ts_run<1, true, false, DVM>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
+    return es ? ts_run<1, false, true, DVM>(c, r, s, llr, max_iter, bits, iters, ok, zout, st)
+              : ts_run<1, false, false, DVM>(c, r, s, llr, max_iter, bits, iters, ok, zout, st);
+  };
+  return L.dvmax <= 8 ? run(std::integral_constant<int, 8>{}) : run(std::integral_constant<int, kDvMax>{});
 }
 
 }  // namespace ldpc
