@@ -30,6 +30,7 @@
 // of every later atomic.
 #include <algorithm>
 
+#include "async_copy.cuh"
 #include "h2_body.cuh"
 #include "kernels.h"
 #include "pp_check.cuh"
@@ -136,24 +137,6 @@ struct Delta {
     return hsub(Ln, Lo);
   }
 };
-
-// Asynchronous global -> shared copies (each lane copies, and later reads, only
-// its own slots, so a lane's wait on its own groups is all the ordering needed).
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ uint2 pack_c8(const NewState& n) {
   return make_uint2((uint32_t)n.al | ((uint32_t)n.ah << 8) | ((uint32_t)n.bl << 16) | ((uint32_t)n.bh << 24),

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "h2_body.cuh"
 #include "kernels.h"
 #include "pp_check.cuh"
@@ -38,6 +39,20 @@ constexpr int kWarps = 8;
 constexpr int kRows = 4;   // checks per warp (horizontal)
 constexpr int kCols = 4;   // variables per warp (vertical)
 constexpr int kDvMax = 16; // column degrees the vertical kernel keeps in registers
+
+// The literal form's vertical scan stages the next variable's inputs (below).
+#ifndef LDPC_TS_VSTAGED
+#define LDPC_TS_VSTAGED 1
+#endif
+constexpr bool kVStaged = LDPC_TS_VSTAGED != 0;
+
+// Per-warp staging of the vertical scan (literal form): the channel word and
+// the message words of one variable per lane, two buffers.
+template <int DVM>
+struct VStage {
+  uint32_t q[2][32];
+  uint32_t l[2][DVM][32];
+};
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -223,6 +238,65 @@ __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s
     }
     return v;
   };
+  if constexpr (FORM2 == 0 && kVStaged) {
+    // literal form: the channel word and the message words of variable t + 1 are
+    // copied into shared memory while variable t computes
+    __shared__ VStage<DVM> vstage[kWarps];
+    VStage<DVM>& vs = vstage[warp];
+    const int nv = n1 - n0;
+    const auto issue = [&](int t) {
+      const int n = n0 + t, b = t & 1;
+      const int e0 = __ldg(c.cptr + n), dv = __ldg(c.cptr + n + 1) - e0;
+      cp_async4(&vs.q[b][lane], s.q0 + (size_t)n * FP + p);
+#pragma unroll
+      for (int a = 0; a < DVM; ++a) {
+        if (a < dv && k > 0) {  // warp-uniform: every lane takes part in the shuffles
+          const uint32_t sl = pick(slw, e0 - ew0 + a);
+          cp_async4(&vs.l[b][a][lane], s.lmn + (size_t)sl * FP + p);
+        }
+      }
+    };
+    issue(0);
+    cp_async_commit();
+    for (int t = 0; t < nv; ++t) {
+      if (t + 1 < nv) issue(t + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      const int n = n0 + t, b = t & 1;
+      const int e0 = __ldg(c.cptr + n), dv = __ldg(c.cptr + n + 1) - e0;
+      const uint32_t q = vs.q[b][lane];
+      uint32_t za = by_to_h2(q), zb = by_to_h2(q >> 16);
+      uint32_t La[DVM], Lb[DVM];
+#pragma unroll
+      for (int a = 0; a < DVM; ++a) {
+        if (a < dv) {
+          const uint32_t l = k > 0 ? vs.l[b][a][lane] : 0x80808080u;  // L = 0 is the byte 128
+          La[a] = k > 0 ? by_to_h2(l) : 0u;
+          Lb[a] = k > 0 ? by_to_h2(l >> 16) : 0u;
+          za = hadd(za, La[a]);
+          zb = hadd(zb, Lb[a]);
+        }
+      }
+      if (post) {
+        uint2* Z = reinterpret_cast<uint2*>(s.zp + (size_t)n * FP + p);
+        uint2 v = make_uint2(za, zb);
+        if ((selA & selB) != kFull) {
+          const uint2 o = __ldcg(Z);
+          v = make_uint2((za & selA) | (o.x & ~selA), (zb & selB) | (o.y & ~selB));
+        }
+        __stcg(Z, v);
+      }
+#pragma unroll
+      for (int a = 0; a < DVM; ++a) {
+        if (a < dv) {
+          const uint32_t sl = pick(slw, e0 - ew0 + a);
+          const uint32_t ba = h2_to_by_sat(hsub(za, La[a])), bb = h2_to_by_sat(hsub(zb, Lb[a]));
+          __stcg(reinterpret_cast<uint32_t*>(s.zmn + (size_t)sl * FP + p), ba | (bb << 16));
+        }
+      }
+    }
+    return;
+  }
   for (int n = n0; n < n1; ++n) {
     const int e0 = __ldg(c.cptr + n), dv = __ldg(c.cptr + n + 1) - e0;
     const uint32_t q = __ldcg(reinterpret_cast<const uint32_t*>(s.q0 + (size_t)n * FP + p));
