@@ -153,6 +153,9 @@ struct TwoScanLayout {
   int dvmax = 16;  // largest column degree of the code (set by the caller; <= 16)
   size_t zmn = 0, lmn = 0, st = 0, q0 = 0, zp = 0, act = 0, fail = 0, iters = 0, ok = 0, total = 0;
 };
+// Sets the staged two-scan vertical kernels' shared-memory attribute on the
+// current device (once per device, outside stream capture).
+cudaError_t twoscan_prepare();
 TwoScanLayout twoscan_layout(int form2, int N, int M, int ell_w, int F);
 bool twoscan_stream_eligible(int N, int M, int ell_w, int max_row_deg, int max_col_deg, int qm, int form2, int F);
 cudaError_t twoscan_stream_decode(const DevCode& c, const IntRule& r, int form2, const TwoScanLayout& L, void* ws,

@@ -444,7 +444,7 @@ ldpc_status ldpc_code_create(ldpc_code** out, int32_t n_vars, int32_t n_checks, 
   }
   // kernel attributes of this device, set here: code creation is never inside
   // a stream capture, and every decode of the code runs on this device
-  if ((err = ldpc::pingpong_prepare()) != cudaSuccess) {
+  if ((err = ldpc::pingpong_prepare()) != cudaSuccess || (err = ldpc::twoscan_prepare()) != cudaSuccess) {
     ldpc_code_destroy(c);
     return cuda_fail(err, "ldpc_code_create kernel attributes");
   }

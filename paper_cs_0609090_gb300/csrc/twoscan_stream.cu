@@ -46,13 +46,17 @@ constexpr int kDvMax = 16; // column degrees the vertical kernel keeps in regist
 #endif
 constexpr bool kVStaged = LDPC_TS_VSTAGED != 0;
 
-// Per-warp staging of the vertical scan (literal form): the channel word and
-// the message words of one variable per lane, two buffers.
-template <int DVM>
+// Per-warp staging of the vertical scan, two buffers: the channel word of one
+// variable per lane and, per edge, the message word (literal form) or the
+// 16-byte state word of the edge's check (Section V messages, 8-byte state).
+template <int FORM2, int DVM>
 struct VStage {
   uint32_t q[2][32];
-  uint32_t l[2][DVM][32];
+  typename std::conditional<FORM2 == 0, uint32_t, uint4>::type l[2][DVM][32];
 };
+// the vertical kernels that stage (the others take no dynamic shared memory)
+template <int FORM2, bool C8, int DVM>
+__host__ __device__ constexpr bool vstaged() { return kVStaged && (FORM2 == 0 || (C8 && DVM == 8)); }
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -238,11 +242,11 @@ __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s
     }
     return v;
   };
-  if constexpr (FORM2 == 0 && kVStaged) {
-    // literal form: the channel word and the message words of variable t + 1 are
-    // copied into shared memory while variable t computes
-    __shared__ VStage<DVM> vstage[kWarps];
-    VStage<DVM>& vs = vstage[warp];
+  if constexpr (vstaged<FORM2, C8, DVM>()) {
+    // the channel word and the message (or check state) words of variable t + 1
+    // are copied into shared memory while variable t computes
+    extern __shared__ __align__(16) unsigned char ts_smem[];
+    VStage<FORM2, DVM>& vs = reinterpret_cast<VStage<FORM2, DVM>*>(ts_smem)[warp];
     const int nv = n1 - n0;
     const auto issue = [&](int t) {
       const int n = n0 + t, b = t & 1;
@@ -251,8 +255,13 @@ __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s
 #pragma unroll
       for (int a = 0; a < DVM; ++a) {
         if (a < dv && k > 0) {  // warp-uniform: every lane takes part in the shuffles
-          const uint32_t sl = pick(slw, e0 - ew0 + a);
-          cp_async4(&vs.l[b][a][lane], s.lmn + (size_t)sl * FP + p);
+          if constexpr (FORM2 == 0) {
+            const uint32_t sl = pick(slw, e0 - ew0 + a);
+            cp_async4(&vs.l[b][a][lane], s.lmn + (size_t)sl * FP + p);
+          } else {
+            const uint32_t m = pick(cjw, e0 - ew0 + a) & 0xffffffu;
+            cp_async16(&vs.l[b][a][lane], s.st + ((size_t)m * FP + p) * 8);
+          }
         }
       }
     };
@@ -270,9 +279,21 @@ __global__ void __launch_bounds__(kWarps * 32) ts_vertical(const DevCode c, TS s
 #pragma unroll
       for (int a = 0; a < DVM; ++a) {
         if (a < dv) {
-          const uint32_t l = k > 0 ? vs.l[b][a][lane] : 0x80808080u;  // L = 0 is the byte 128
-          La[a] = k > 0 ? by_to_h2(l) : 0u;
-          Lb[a] = k > 0 ? by_to_h2(l >> 16) : 0u;
+          if (k == 0) {
+            La[a] = 0u;
+            Lb[a] = 0u;
+          } else if constexpr (FORM2 == 0) {
+            const uint32_t l = vs.l[b][a][lane];
+            La[a] = by_to_h2(l);
+            Lb[a] = by_to_h2(l >> 16);
+          } else {
+            const uint32_t j = pick(cjw, e0 - ew0 + a) >> 24;
+            const uint4 u = vs.l[b][a][lane];
+            const SV oa = SVUnit<true>::unpack(make_uint2(u.x, u.y)), ob = SVUnit<true>::unpack(make_uint2(u.z, u.w));
+            const uint32_t jh = small_to_h2((int32_t)j, (int32_t)j);
+            La[a] = hfma(hsub(oa.B, oa.A), heq_one(oa.I, jh), oa.A) ^ ((oa.S << j) & 0x80008000u);
+            Lb[a] = hfma(hsub(ob.B, ob.A), heq_one(ob.I, jh), ob.A) ^ ((ob.S << j) & 0x80008000u);
+          }
           za = hadd(za, La[a]);
           zb = hadd(zb, Lb[a]);
         }
@@ -476,10 +497,11 @@ cudaError_t ts_run(const DevCode& c, const IntRule& r, const TS& s, const int8_t
   const dim3 hgrid((unsigned)((c.M + kWarps * kRows - 1) / (kWarps * kRows)), (unsigned)(s.FP / 64));
   const dim3 vgrid((unsigned)((c.N + kWarps * kCols - 1) / (kWarps * kCols)), (unsigned)(s.FP / 64));
   ts_init<ES><<<tgrid, 256, 0, st>>>(c, llr, s, K);
-  ts_vertical<FORM2, C8, ES, DVM><<<vgrid, kWarps * 32, 0, st>>>(c, s, 0, (ES || K == 0) ? 1 : 0);
+  const size_t vsm = vstaged<FORM2, C8, DVM>() ? sizeof(VStage<FORM2, DVM>) * kWarps : 0;
+  ts_vertical<FORM2, C8, ES, DVM><<<vgrid, kWarps * 32, vsm, st>>>(c, s, 0, (ES || K == 0) ? 1 : 0);
   for (int k = 1; k <= K; ++k) {
     ts_horizontal<FORM2, C8, ES><<<hgrid, kWarps * 32, 0, st>>>(c, r, s, k);
-    ts_vertical<FORM2, C8, ES, DVM><<<vgrid, kWarps * 32, 0, st>>>(c, s, k, (ES || k == K) ? 1 : 0);
+    ts_vertical<FORM2, C8, ES, DVM><<<vgrid, kWarps * 32, vsm, st>>>(c, s, k, (ES || k == K) ? 1 : 0);
   }
   ts_final<ES><<<hgrid, kWarps * 32, 0, st>>>(c, s, K);
   ts_output<<<tgrid, 256, 0, st>>>(c, s, K, bits, iters, ok, zout);
@@ -487,6 +509,18 @@ cudaError_t ts_run(const DevCode& c, const IntRule& r, const TS& s, const int8_t
 }
 
 }  // namespace
+
+cudaError_t twoscan_prepare() {
+  // the staged vertical kernels of the Section V-message form take more than
+  // the default 48 KB of dynamic shared memory; set on the current device
+  // outside any stream capture (code creation)
+  for (auto f : {ts_vertical<1, true, false, 8>, ts_vertical<1, true, true, 8>}) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(VStage<1, 8>) * kWarps));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 TwoScanLayout twoscan_layout(int form2, int N, int M, int ell_w, int F) {
   TwoScanLayout L;
