@@ -45,6 +45,11 @@ constexpr int kDvMax = 16; // column degrees the vertical kernel keeps in regist
 #define LDPC_TS_VSTAGED 1
 #endif
 constexpr bool kVStaged = LDPC_TS_VSTAGED != 0;
+// ... and the horizontal scan the next check's Z_mn words (without early stop)
+#ifndef LDPC_TS_HSTAGED
+#define LDPC_TS_HSTAGED 1
+#endif
+constexpr bool kHStaged = LDPC_TS_HSTAGED != 0;
 
 // Per-warp staging of the vertical scan, two buffers: the channel word of one
 // variable per lane and, per edge, the message word (literal form) or the
@@ -101,14 +106,15 @@ __device__ __forceinline__ uint32_t running(const TS& s, int k, int p) {
 // first pair, 2-3 second) from the posteriors at the handles h[j].
 template <int FORM2, bool C8, bool ES, int D, int DMAX>
 __device__ __forceinline__ uint32_t ts_check(const TS& s, int m, int d, int M, int p, const uint32_t* h,
-                                             const H2Rule& rule, uint32_t ksat) {
+                                             const H2Rule& rule, uint32_t ksat, const uint32_t* zin = nullptr) {
   constexpr int NJ = D > 0 ? D : DMAX;
   const int FP = s.FP;
   uint32_t K1a = ksat, K2a = ksat, NEGa = 0, K1b = ksat, K2b = ksat, NEGb = 0, Ya = 0, Yb = 0;
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     if (D > 0 || j < d) {
-      const uint32_t z = __ldcg(reinterpret_cast<const uint32_t*>(s.zmn + (size_t)(j * M + m) * FP + p));
+      // the check's Z_mn words: staged by the caller (zin), else read here
+      const uint32_t z = zin ? zin[j] : __ldcg(reinterpret_cast<const uint32_t*>(s.zmn + (size_t)(j * M + m) * FP + p));
       key_step(by_to_h2(z), j, K1a, K2a, NEGa);
       key_step(by_to_h2(z >> 16), j, K1b, K2b, NEGb);
       if (ES) {
@@ -160,6 +166,31 @@ __global__ void __launch_bounds__(kWarps * 32) ts_horizontal(const DevCode c, co
   const int m1 = min(m0 + kRows, c.M);
   const int DM = (FORM2 == 1 && C8) ? 8 : 16;
   uint32_t fail = 0;
+  if (kHStaged && !ES && m1 - m0 == kRows && c.deg(m0) == c.deg(m1 - 1) && (c.deg(m0) == 6 || c.deg(m0) == 7)) {
+    // checks of one degree (6 or 7) without early stop: the Z_mn words of check
+    // r + 1 are copied into shared memory while check r computes
+    __shared__ uint32_t hz[kWarps][2][7][32];
+    const int d = c.deg(m0);
+    const auto issue = [&](int r) {
+      for (int j = 0; j < d; ++j)
+        cp_async4(&hz[warp][r & 1][j][lane], s.zmn + (size_t)(j * c.M + m0 + r) * s.FP + p);
+    };
+    issue(0);
+    cp_async_commit();
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+      if (r + 1 < kRows) issue(r + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      uint32_t z[7];
+#pragma unroll
+      for (int j = 0; j < 7; ++j) z[j] = hz[warp][r & 1][j][lane];
+      uint32_t h[16];
+      if (d == 6) ts_check<FORM2, C8, ES, 6, 6>(s, m0 + r, d, c.M, p, h, rule, ksat, z);
+      else ts_check<FORM2, C8, ES, 7, 7>(s, m0 + r, d, c.M, p, h, rule, ksat, z);
+    }
+    return;
+  }
   for (int m = m0; m < m1; ++m) {
     const int d = c.deg(m);
     uint32_t h[16];
