@@ -24,6 +24,7 @@
 #include "h2ops.cuh"
 #include "kernels.h"
 #include "launch_util.h"
+#include "pp_check.cuh"
 
 namespace ldpc {
 namespace {
@@ -64,20 +65,23 @@ __device__ __forceinline__ int32_t ts_q0(const int8_t* __restrict__ llr, int32_t
   return f < F ? (int32_t)__ldg(llr + (size_t)f * N + n) : 0;
 }
 
-// Horizontal scan of check m, Eq. (1), for the G frames.  Returns the decision
+// Horizontal scan of check m, Eq. (1), for the G frames: the min-search key
+// (16 |Z_mn| + j) 2^-11 of one saturating multiply-add per position, with the
+// minima started at the key of Qm (so that they decode to 16 min(|Z_mn|, Qm) +
+// j), the rule and the signs as in the single-scan kernels (key_step,
+// finish_state), L_mn written back into the cells.  Returns the decision
 // parity bits of x^(k-1) (from Zp) when ES.
 template <int G, int DMAX, bool ES>
-__device__ __forceinline__ uint32_t ts_horizontal(const DevCode& c, const IntRule& r, uint32_t qm2, int m,
+__device__ __forceinline__ uint32_t ts_horizontal(const DevCode& c, const H2Rule& rule, uint32_t ksat, int m,
                                                   uint32_t* __restrict__ Cell, const uint32_t* __restrict__ Zp) {
   constexpr int P = G / 2;
   const int M = c.M;
   const int d = c.deg(m);
-  uint32_t K1[P], K2[P], X[P], NEG[P], Y[P];
+  uint32_t K1[P], K2[P], NEG[P], Y[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    K1[p] = h2c(2048);
-    K2[p] = h2c(2048);
-    X[p] = 0;
+    K1[p] = ksat;
+    K2[p] = ksat;
     NEG[p] = 0;
     Y[p] = 0;
   }
@@ -93,25 +97,18 @@ __device__ __forceinline__ uint32_t ts_horizontal(const DevCode& c, const IntRul
         for (int p = 0; p < P; ++p) Y[p] ^= dec_bits(w[p]);
       }
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        X[p] ^= z[p];
-        NEG[p] |= (z[p] & 0x80008000u) >> (15 - j);
-        const uint32_t key = hfma(hmin(habs(z[p]), qm2), h2c(16), h2c(j));
-        K2[p] = hmin(K2[p], hmax(K1[p], key));
-        K1[p] = hmin(K1[p], key);
-      }
+      for (int p = 0; p < P; ++p) key_step(z[p], j, K1[p], K2[p], NEG[p]);
     }
   }
-  uint32_t An[P], Bn[P], In[P], Sn[P];
   uint32_t par = 0;
+  uint32_t An[P], Dn[P], In[P], SN[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    Sn[p] = NEG[p] ^ prmt(X[p], 0u, 0xBB99u);
-    const int32_t k1l = h_lo_int(K1[p]), k1h = h_hi_int(K1[p]);
-    const int32_t k2l = h_lo_int(K2[p]), k2h = h_hi_int(K2[p]);
-    An[p] = small_to_h2(r.g(k1l >> 4), r.g(k1h >> 4));
-    Bn[p] = small_to_h2(r.g(k2l >> 4), r.g(k2h >> 4));
-    In[p] = small_to_h2(k1l & 15, k1h & 15);
+    const NewState n = finish_state(K1[p], K2[p], NEG[p], d, rule);
+    An[p] = n.An;
+    Dn[p] = hsub(n.Bn, n.An);
+    In[p] = n.In;
+    SN[p] = n.Sn;
     if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
   }
 #pragma unroll
@@ -120,9 +117,9 @@ __device__ __forceinline__ uint32_t ts_horizontal(const DevCode& c, const IntRul
       uint32_t l[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const uint32_t msk = heq_mask(In[p], h2c(j));
-        const uint32_t mag = (Bn[p] & msk) | (An[p] & ~msk);
-        l[p] = mag ^ ((Sn[p] << (15 - j)) & 0x80008000u);
+        // f(A, B, n, n~) = A + (B - A) [j = n~], the sign on the binary16 sign bit
+        l[p] = hfma(Dn[p], heq_one(In[p], h2c(j)), An[p]) ^ (SN[p] & 0x80008000u);
+        SN[p] += SN[p];
       }
       ts_st<G>(Cell, (size_t)j * M + m, l);
     }
@@ -170,6 +167,9 @@ onchip_twoscan_kernel(const DevCode c, const IntRule r, const int8_t* __restrict
   const int tid = threadIdx.x, nt = blockDim.x;
   const int N8 = (N + 7) >> 3;
   const uint32_t qm2 = ints_to_h2(r.qm, r.qm);
+  const H2Rule hr = make_h2rule(r);
+  // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
+  const uint32_t ksat = hfma(qm2, h2c_q11(16), h2c_q11(15));
 
   for (int grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
     const int f0 = grp * G;
@@ -198,7 +198,7 @@ onchip_twoscan_kernel(const DevCode c, const IntRule r, const int8_t* __restrict
     for (int k = 1; k <= max_iter && act != 0u; ++k) {
       const int kp = k & 1;
       uint32_t fail = 0;
-      for (int m = tid; m < M; m += nt) fail |= ts_horizontal<G, DMAX, ES>(c, r, qm2, m, Cell, Zp);
+      for (int m = tid; m < M; m += nt) fail |= ts_horizontal<G, DMAX, ES>(c, hr, ksat, m, Cell, Zp);
       if constexpr (ES) {
         fail = __reduce_or_sync(0xffffffffu, fail);
         if ((tid & 31) == 0 && (fail & act)) atomicOr(&s_fail[kp], fail & act);
@@ -206,25 +206,54 @@ onchip_twoscan_kernel(const DevCode c, const IntRule r, const int8_t* __restrict
       __syncthreads();
       const uint32_t stop = ES ? (act & ~s_fail[kp]) : 0u;
       const uint32_t cont = act & ~stop;
+      constexpr int kTsDv = G == 2 ? 16 : 8;  // column degrees the vertical scan unrolls
       for (int n = tid; n < N; n += nt) {
         const int a0 = __ldg(c.cptr + n), a1 = __ldg(c.cptr + n + 1);
         uint32_t S[P];
 #pragma unroll
         for (int p = 0; p < P; ++p)
           S[p] = ints_to_h2(ts_q0(llr, N, f0 + 2 * p, F, n), ts_q0(llr, N, f0 + 2 * p + 1, F, n));
-        for (int a = a0; a < a1; ++a) {
-          uint32_t l[P];
-          ts_ld<G>(Cell, (size_t)__ldg(c.cslot + a), l);
+        if (a1 - a0 <= kTsDv) {
+          // unrolled over the column degree: the slot indices of all the
+          // variable's edges are loaded together, then their cells, instead of
+          // one index -> cell chain per edge
+          const int dv = a1 - a0;
+          uint32_t sl[kTsDv], lv[kTsDv][P];
 #pragma unroll
-          for (int p = 0; p < P; ++p) S[p] = hadd(S[p], l[p]);
-        }
-        for (int a = a0; a < a1; ++a) {
-          const size_t sl = (size_t)__ldg(c.cslot + a);
-          uint32_t l[P];
-          ts_ld<G>(Cell, sl, l);
+          for (int a = 0; a < kTsDv; ++a)
+            if (a < dv) sl[a] = (uint32_t)__ldg(c.cslot + a0 + a);
 #pragma unroll
-          for (int p = 0; p < P; ++p) l[p] = hsub(S[p], l[p]);
-          ts_st<G>(Cell, sl, l);
+          for (int a = 0; a < kTsDv; ++a) {
+            if (a < dv) {
+              ts_ld<G>(Cell, sl[a], lv[a]);
+#pragma unroll
+              for (int p = 0; p < P; ++p) S[p] = hadd(S[p], lv[a][p]);
+            }
+          }
+#pragma unroll
+          for (int a = 0; a < kTsDv; ++a) {
+            if (a < dv) {
+              uint32_t l[P];
+#pragma unroll
+              for (int p = 0; p < P; ++p) l[p] = hsub(S[p], lv[a][p]);
+              ts_st<G>(Cell, sl[a], l);
+            }
+          }
+        } else {
+          for (int a = a0; a < a1; ++a) {
+            uint32_t l[P];
+            ts_ld<G>(Cell, (size_t)__ldg(c.cslot + a), l);
+#pragma unroll
+            for (int p = 0; p < P; ++p) S[p] = hadd(S[p], l[p]);
+          }
+          for (int a = a0; a < a1; ++a) {
+            const size_t sl = (size_t)__ldg(c.cslot + a);
+            uint32_t l[P];
+            ts_ld<G>(Cell, sl, l);
+#pragma unroll
+            for (int p = 0; p < P; ++p) l[p] = hsub(S[p], l[p]);
+            ts_st<G>(Cell, sl, l);
+          }
         }
         uint32_t w[P];
         ts_ld<G>(Zp, n, w);
