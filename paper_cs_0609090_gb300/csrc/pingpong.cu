@@ -117,31 +117,103 @@ __device__ __forceinline__ void red_add_h2x2(uint32_t* p, uint32_t a, uint32_t b
   asm volatile("red.global.add.noftz.v2.f16x2 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b));
 }
 
+// Section V state of one check and frame pair as the row pass reads it: A and
+// B - A as binary16 values, n~ as the pattern of 1024 + n~ (compared with
+// 1024 + j), and the sign word.  The stored bytes become patterns 1024 + v with
+// one byte permute each.
+struct SVD {
+  uint32_t A, D, Ip, S;
+};
+__device__ __forceinline__ SVD unpack_d(uint32_t x, uint32_t y) {
+  const uint32_t Ap = __byte_perm(x, 0x64u, 0x4140), Bp = __byte_perm(x, 0x64u, 0x4342);
+  return SVD{hsub(Ap, h2c(1024)), hsub(Bp, Ap), __byte_perm(y, 0x64u, 0x4240), y};
+}
+
+// [j = n~] as 1.0 / 0.0 from the pattern of 1024 + n~: a set instruction (ALU
+// pipe), or sat(1 - |n~ - j|) with two FMA-pipe instructions (kEqFma)
+__device__ __forceinline__ uint32_t pos_ind(uint32_t Ip, int j) {
+  if constexpr (kEqFma) return hfma_sat(hab(hsub(Ip, h2c(1024 + j))), 0xBC00BC00u, 0x3C003C00u);
+  else return heq_one(Ip, h2c(1024 + j));
+}
+
+// The new state of one check and frame pair from the keys K1, K2 = (16 m + j)
+// 2^-11 of the two minima (j <= 7) and the sign bits NEG, all in binary16
+// pairs.  1024 + 128 K rounds to the integer 1024 + m (j / 16 < 1/2), and
+// 2048 K + (1024 - 16 m) = 1024 + j gives n~.  The rule g (Section III) acts
+// on these patterns: the offset as max(1024 - beta + 128 K, 1024), again
+// rounding away j / 16; the normalized scaling floor(m num / 2^shift) on the
+// integer halves of the pattern, whose low 10 bits hold m.  A pattern 1024 + v
+// (v < 256) keeps v in its low byte, so the stored bytes are byte permutes.
+struct NewD {
+  uint32_t An, Dn, Ip, Sn;  // A, B - A (values), 1024 + n~ (pattern), signs
+  uint2 st;                 // the 8-byte stored state (pack layout of SVUnit<true>)
+};
+struct FinArgs {
+  uint32_t cb;         // pair of 1024 - beta (offset rule)
+  uint32_t num, shift; // normalized rule
+};
+template <bool NORM>
+__device__ __forceinline__ NewD finish_d(uint32_t K1, uint32_t K2, uint32_t NEG, int dd, const FinArgs& f) {
+  NewD n;
+  const uint32_t dlane = ((1u << dd) - 1u) << (16 - dd);  // bits 16-d .. 15
+  const uint32_t pm = ((__popc(NEG & 0xffffu) & 1) ? 0x0000ffffu : 0u) | ((__popc(NEG >> 16) & 1) ? 0xffff0000u : 0u);
+  n.Sn = (NEG ^ pm) & (dlane | (dlane << 16));
+  const uint32_t M1 = hfma(K1, h2c(128), h2c(1024));                               // 1024 + m1
+  n.Ip = hfma(K1, h2c(2048), hfma(M1, h2c(16) | 0x80008000u, h2c(17408)));         // 1024 + n~
+  uint32_t Ap, Bp;
+  if constexpr (NORM) {
+    const uint32_t M2 = hfma(K2, h2c(128), h2c(1024));
+    Ap = __byte_perm(((M1 & 0x03ff03ffu) * f.num) >> f.shift, 0x64u, 0x4240);
+    Bp = __byte_perm(((M2 & 0x03ff03ffu) * f.num) >> f.shift, 0x64u, 0x4240);
+  } else {
+    Ap = hmax(hfma(K1, h2c(128), f.cb), h2c(1024));
+    Bp = hmax(hfma(K2, h2c(128), f.cb), h2c(1024));
+  }
+  n.An = hsub(Ap, h2c(1024));
+  n.Dn = hsub(Bp, Ap);
+  n.st = make_uint2(__byte_perm(Ap, Bp, 0x6420), (n.Ip & 0x00ff00ffu) | (n.Sn & 0xff00ff00u));
+  return n;
+}
+
+// Pass 1 of one check (Section IV Eq. (3)) on the state of iteration k-1:
+// u_j = Z_j - L^(k-1)_j with L rebuilt as A + (B - A) [j = n~] under the sign
+// bit, minima keys and sign bits (key_step), and the decision parity of
+// x^(k-1) (bit 0 even frame, bit 1 odd frame) when ES.
+template <int D, bool ES>
+__device__ __forceinline__ void pass1_d(const uint32_t* w, int d, const SVD& o, uint32_t ksat, uint32_t two,
+                                        uint32_t& K1, uint32_t& K2, uint32_t& NEG, uint32_t& par) {
+  constexpr int NJ = D > 0 ? D : 8;
+  K1 = ksat;
+  K2 = ksat;
+  NEG = 0;
+  uint32_t Y = 0, SR = o.S;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (D > 0 || j < d) {
+      const uint32_t L = hfma(o.D, pos_ind(o.Ip, j), o.A) ^ (SR & 0x80008000u);
+      SR *= two;
+      const uint32_t u = hsub(w[j], L);
+      if (ES) Y ^= dec_bits(w[j]);
+      key_step(u, j, K1, K2, NEG);
+    }
+  }
+  if (ES) par = ((Y >> 15) & 1u) | ((Y >> 30) & 2u);
+}
+
 // L^(k)_j - L^(k-2)_j for successive positions j of one check and frame pair.
 struct Delta {
-  uint32_t An, Dn, In, SN;  // iteration k: A, B - A, n~, signs (shifted as j advances)
+  uint32_t An, Dn, In, SN;  // iteration k: A, B - A, 1024 + n~, signs (shifted as j advances)
   uint32_t Ao, Do, Io, SO;  // iteration k-2
-  __device__ __forceinline__ Delta(const NewState& n, const SV& o)
-      : An(n.An), Dn(hsub(n.Bn, n.An)), In(n.In), SN(n.Sn), Ao(o.A), Do(hsub(o.B, o.A)), Io(o.I), SO(o.S) {}
-  // [j = n~] as 1.0 / 0.0: a set instruction (ALU pipe), or sat(1 - |n~ - j|)
-  // with two FMA-pipe instructions (kEqFma), which the ALU-bound pass prefers
-  __device__ __forceinline__ static uint32_t ind(uint32_t I, int j) {
-    if constexpr (kEqFma) return hfma_sat(hab(hsub(I, h2c(j))), 0xBC00BC00u, 0x3C003C00u);
-    else return heq_one(I, h2c(j));
-  }
+  __device__ __forceinline__ Delta(const NewD& n, const SVD& o)
+      : An(n.An), Dn(n.Dn), In(n.Ip), SN(n.Sn), Ao(o.A), Do(o.D), Io(o.Ip), SO(o.S) {}
   __device__ __forceinline__ uint32_t next(int j, uint32_t two) {
-    const uint32_t Ln = hfma(Dn, ind(In, j), An) ^ (SN & 0x80008000u);
-    const uint32_t Lo = hfma(Do, ind(Io, j), Ao) ^ (SO & 0x80008000u);
+    const uint32_t Ln = hfma(Dn, pos_ind(In, j), An) ^ (SN & 0x80008000u);
+    const uint32_t Lo = hfma(Do, pos_ind(Io, j), Ao) ^ (SO & 0x80008000u);
     SN *= two;
     SO *= two;
     return hsub(Ln, Lo);
   }
 };
-
-__device__ __forceinline__ uint2 pack_c8(const NewState& n) {
-  return make_uint2((uint32_t)n.al | ((uint32_t)n.ah << 8) | ((uint32_t)n.bl << 16) | ((uint32_t)n.bh << 24),
-                    (uint32_t)n.il | ((uint32_t)n.ih << 16) | (n.Sn & 0xff00ff00u));
-}
 
 struct RowArgs {
   const uint32_t* Zr;  // Z^(k-1) at the lane's first pair
@@ -150,27 +222,28 @@ struct RowArgs {
   char* S2;            // state of k-2, overwritten with k
   uint32_t FP, M;
   uint32_t amA, amB;   // running halves of the lane's two pairs
-  uint32_t ksat;
+  uint32_t ksat;       // (16 Qm + 7) 2^-11: the largest key of a magnitude saturated to Qm
   uint32_t two;        // 2, doubling the running sign words (see sv_pass1)
-  H2Rule rule;
+  FinArgs fin;
 };
 
 // The Section V check from its inputs: posteriors wa / wb of the lane's two
 // pairs at the check's positions, the 16-byte state words of iterations k-1
 // (s1) and k-2 (s2).  Adds L^(k) - L^(k-2) at the handles h[j] and overwrites
 // the k-2 state with the new one.  Returns the decision parities as check2.
-template <bool ES, int D>
+template <bool ES, bool NORM, int D>
 __device__ __forceinline__ uint32_t check2_sv(const RowArgs& x, int m, int d, const uint32_t* h, const uint32_t* wa,
                                               const uint32_t* wb, uint4 s1, uint4 s2) {
   constexpr int NJ = D > 0 ? D : 8;
   uint32_t pa = 0, pb = 0;
   const uint32_t two = kShiftFma ? x.two : 2u;
-  const NewState na =
-      sv_pass1<D, 8, ES>(wa, d, SVUnit<true>::unpack(make_uint2(s1.x, s1.y)), x.rule, x.ksat, pa, two);
-  const NewState nb =
-      sv_pass1<D, 8, ES>(wb, d, SVUnit<true>::unpack(make_uint2(s1.z, s1.w)), x.rule, x.ksat, pb, two);
-  Delta ga(na, SVUnit<true>::unpack(make_uint2(s2.x, s2.y)));
-  Delta gb(nb, SVUnit<true>::unpack(make_uint2(s2.z, s2.w)));
+  uint32_t K1a, K2a, NEGa, K1b, K2b, NEGb;
+  pass1_d<D, ES>(wa, d, unpack_d(s1.x, s1.y), x.ksat, two, K1a, K2a, NEGa, pa);
+  pass1_d<D, ES>(wb, d, unpack_d(s1.z, s1.w), x.ksat, two, K1b, K2b, NEGb, pb);
+  const int dd = D > 0 ? D : d;
+  const NewD na = finish_d<NORM>(K1a, K2a, NEGa, dd, x.fin), nb = finish_d<NORM>(K1b, K2b, NEGb, dd, x.fin);
+  Delta ga(na, unpack_d(s2.x, s2.y));
+  Delta gb(nb, unpack_d(s2.z, s2.w));
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     if (D > 0 || j < d) {
@@ -181,8 +254,7 @@ __device__ __forceinline__ uint32_t check2_sv(const RowArgs& x, int m, int d, co
       if (!ES || (x.amA | x.amB) != 0u) red_add_h2x2(x.Za + h[j], da, db);
     }
   }
-  const uint2 ua = pack_c8(na), ub = pack_c8(nb);
-  __stcg(reinterpret_cast<uint4*>(x.S2 + (size_t)m * x.FP * 8), make_uint4(ua.x, ua.y, ub.x, ub.y));
+  __stcg(reinterpret_cast<uint4*>(x.S2 + (size_t)m * x.FP * 8), make_uint4(na.st.x, na.st.y, nb.st.x, nb.st.y));
   return pa | (pb << 2);
 }
 
@@ -190,7 +262,7 @@ __device__ __forceinline__ uint32_t check2_sv(const RowArgs& x, int m, int d, co
 // pairs, the per-edge byte pairs of iterations k-1 (l1) and k-2 (l2) at each
 // position.  Adds L^(k) - L^(k-2) at the handles h[j] and overwrites the k-2
 // slots with L^(k).  Returns the decision parities as check2.
-template <bool ES, int D>
+template <bool ES, bool NORM, int D>
 __device__ __forceinline__ uint32_t check2_pe(const RowArgs& x, int m, int d, const uint32_t* h, const uint32_t* wa,
                                               const uint32_t* wb, const uint32_t* l1, const uint32_t* l2) {
   constexpr int NJ = D > 0 ? D : 8;
@@ -208,14 +280,13 @@ __device__ __forceinline__ uint32_t check2_pe(const RowArgs& x, int m, int d, co
     }
   }
   const int dd = D > 0 ? D : d;
-  const NewState na = finish_state(K1a, K2a, NEGa, dd, x.rule), nb = finish_state(K1b, K2b, NEGb, dd, x.rule);
-  const uint32_t Dna = hsub(na.Bn, na.An), Dnb = hsub(nb.Bn, nb.An);
+  const NewD na = finish_d<NORM>(K1a, K2a, NEGa, dd, x.fin), nb = finish_d<NORM>(K1b, K2b, NEGb, dd, x.fin);
   uint32_t SNa = na.Sn, SNb = nb.Sn;
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     if (D > 0 || j < d) {
-      const uint32_t La = hfma(Dna, heq_one(na.In, h2c(j)), na.An) ^ (SNa & 0x80008000u);
-      const uint32_t Lb = hfma(Dnb, heq_one(nb.In, h2c(j)), nb.An) ^ (SNb & 0x80008000u);
+      const uint32_t La = hfma(na.Dn, pos_ind(na.Ip, j), na.An) ^ (SNa & 0x80008000u);
+      const uint32_t Lb = hfma(nb.Dn, pos_ind(nb.Ip, j), nb.An) ^ (SNb & 0x80008000u);
       SNa += SNa;
       SNb += SNb;
       const uint32_t da = ES ? hsub(La, pe_to_h2(l2[j] & 0xffffu)) & x.amA : hsub(La, pe_to_h2(l2[j] & 0xffffu));
@@ -234,7 +305,7 @@ __device__ __forceinline__ uint32_t check2_pe(const RowArgs& x, int m, int d, co
 // One check m of degree d (D > 0: exactly D) for the lane's two pairs, handles
 // h[j] (variable x FP).  Returns the decision parities of x^(k-1) of both pairs
 // (bits 0-1 first pair, 2-3 second).
-template <int FORM, bool ES, int D>
+template <int FORM, bool ES, bool NORM, int D>
 __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const uint32_t* h) {
   constexpr int NJ = D > 0 ? D : 8;
   uint32_t wa[NJ], wb[NJ];
@@ -250,7 +321,7 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
     const size_t so = (size_t)m * x.FP * 8;
     const uint4 s1 = __ldcg(reinterpret_cast<const uint4*>(x.S1 + so));
     const uint4 s2 = __ldcg(reinterpret_cast<const uint4*>(x.S2 + so));
-    return check2_sv<ES, D>(x, m, d, h, wa, wb, s1, s2);
+    return check2_sv<ES, NORM, D>(x, m, d, h, wa, wb, s1, s2);
   } else {
     // per-edge: slot j M + m holds the byte pairs of both pairs in one word
     uint32_t l1[NJ], l2[NJ];
@@ -262,7 +333,7 @@ __device__ __forceinline__ uint32_t check2(const RowArgs& x, int m, int d, const
         l2[j] = __ldcg(reinterpret_cast<const uint32_t*>(x.S2 + so));
       }
     }
-    return check2_pe<ES, D>(x, m, d, h, wa, wb, l1, l2);
+    return check2_pe<ES, NORM, D>(x, m, d, h, wa, wb, l1, l2);
   }
 }
 
@@ -292,7 +363,7 @@ struct Stage<0> {  // posterior pairs and the k-1 / k-2 message words of each po
 // per-edge staging: 57,344 bytes per 8-warp CTA, so that 4 CTAs with their
 // 1 KB reservations fill the SM's 233,472 bytes exactly
 
-template <int FORM, bool ES, int D>
+template <int FORM, bool ES, bool NORM, int D>
 __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const uint32_t* hl, int lane,
                                                 Stage<FORM>& sg) {
   constexpr int T = kRows * kGroups;
@@ -336,7 +407,7 @@ __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const 
       wb[j] = v.y;
     }
     if constexpr (FORM == 1) {
-      fail |= check2_sv<ES, D>(x, m0 + t, D, h, wa, wb, sg.s[b][0][lane], sg.s[b][1][lane]);
+      fail |= check2_sv<ES, NORM, D>(x, m0 + t, D, h, wa, wb, sg.s[b][0][lane], sg.s[b][1][lane]);
     } else {
       uint32_t l1[D], l2[D];
 #pragma unroll
@@ -344,7 +415,7 @@ __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const 
         l1[j] = sg.l1[b][j][lane];
         l2[j] = sg.l2[b][j][lane];
       }
-      fail |= check2_pe<ES, D>(x, m0 + t, D, h, wa, wb, l1, l2);
+      fail |= check2_pe<ES, NORM, D>(x, m0 + t, D, h, wa, wb, l1, l2);
     }
   }
   return fail;
@@ -353,7 +424,7 @@ __device__ __forceinline__ uint32_t rows_staged(const RowArgs& x, int m0, const 
 // Row kernel of iteration k: block (bx, chunk) of nw warps takes nw kRows
 // kGroups checks of the degree-sorted order for the chunk's 64 pairs (warp w:
 // checks (bx nw + w) kRows kGroups ..., lane l: pairs chunk 64 + 2 l, + 1).
-template <int FORM, bool ES>
+template <int FORM, bool ES, bool NORM>
 // CTAs per SM (registers 65536 / (256 x LDPC_PP2_MINB1 or _MINB0)), measured on
 // the N=64800 code: Section V with staged inputs 4 (7.83 ms, 52 bytes of spills,
 // against 8.16 ms at 3 without spills; 5 spills 436 bytes); per edge 3.
@@ -395,9 +466,14 @@ pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
   x.M = (uint32_t)c.M;
   x.amA = half_mask(aA);
   x.amB = half_mask(aB);
-  x.rule = make_h2rule(ir);
-  // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
-  x.ksat = hfma(ints_to_h2(ir.qm, ir.qm), h2c_q11(16), h2c_q11(15));
+  // offset rule (beta <= 127): 1024 - beta; normalized: num / 2^shift; plain: neither
+  const int beta = ir.rule == 1 ? ir.beta : 0;
+  x.fin.cb = ints_to_h2(1024 - beta, 1024 - beta);
+  x.fin.num = (uint32_t)ir.num;
+  x.fin.shift = (uint32_t)ir.shift;
+  // (16 Qm + 7) 2^-11: the key of a magnitude saturated to Qm at position 7
+  // (every position of these checks is <= 7, so the minima decode above holds)
+  x.ksat = hfma(ints_to_h2(ir.qm, ir.qm), h2c_q11(16), h2c_q11(7));
   x.two = s.two;
   const int nw = blockDim.x >> 5;
   const int m0 = (blockIdx.x * nw + warp) * kRows * kGroups;
@@ -421,7 +497,8 @@ pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
     if constexpr (FORM == 1 || LDPC_PP2_STAGED_PE) {
       extern __shared__ __align__(16) unsigned char pp2_smem[];
       Stage<FORM>& sg = reinterpret_cast<Stage<FORM>*>(pp2_smem)[warp];
-      fail = d0 == 6 ? rows_staged<FORM, ES, 6>(x, m0, hl, lane, sg) : rows_staged<FORM, ES, 7>(x, m0, hl, lane, sg);
+      fail = d0 == 6 ? rows_staged<FORM, ES, NORM, 6>(x, m0, hl, lane, sg)
+                     : rows_staged<FORM, ES, NORM, 7>(x, m0, hl, lane, sg);
     } else
 #endif
 #pragma unroll
@@ -431,11 +508,11 @@ pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
       if (d0 == 6) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) h[j] = __shfl_sync(kFull, hl[g], r * 6 + j);
-        fail |= check2<FORM, ES, 6>(x, m0 + t, 6, h);
+        fail |= check2<FORM, ES, NORM, 6>(x, m0 + t, 6, h);
       } else {
 #pragma unroll
         for (int j = 0; j < 7; ++j) h[j] = __shfl_sync(kFull, hl[g], r * 7 + j);
-        fail |= check2<FORM, ES, 7>(x, m0 + t, 7, h);
+        fail |= check2<FORM, ES, NORM, 7>(x, m0 + t, 7, h);
       }
     }
   } else {
@@ -445,7 +522,7 @@ pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
 #pragma unroll
       for (int j = 0; j < 8; ++j)
         if (j < d) h[j] = (uint32_t)c.col(j, m) * x.FP;
-      fail |= check2<FORM, ES, 0>(x, m, d, h);
+      fail |= check2<FORM, ES, NORM, 0>(x, m, d, h);
     }
   }
   if (ES) {
@@ -630,7 +707,9 @@ cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, int warps,
   const dim3 rgrid_rows((unsigned)((c.M + row_tile - 1) / row_tile), (unsigned)(s.FP / 64));
   pp2_init<ES><<<tgrid, 256, 0, st>>>(c, llr, s, K);
   const size_t smem = LDPC_PP2_STAGED && (FORM == 1 || LDPC_PP2_STAGED_PE) ? sizeof(Stage<FORM>) * warps : 0;
-  for (int k = 1; k <= K; ++k) pp2_rows<FORM, ES><<<rgrid_rows, warps * 32, smem, st>>>(c, r, s, k);
+  // the normalized rule scales integer halves, the offset and plain rules take max(., 1024)
+  const auto rows = r.rule == 2 ? pp2_rows<FORM, ES, true> : pp2_rows<FORM, ES, false>;
+  for (int k = 1; k <= K; ++k) rows<<<rgrid_rows, warps * 32, smem, st>>>(c, r, s, k);
   pp2_final<ES><<<rgrid, kWarps * 32, 0, st>>>(c, s, K);
   pp2_output<<<tgrid, 256, 0, st>>>(c, s, K, bits, iters, ok, zout);
   return cudaGetLastError();
@@ -641,12 +720,12 @@ cudaError_t pp2_run(const DevCode& c, const IntRule& r, const PP2& s, int warps,
 cudaError_t pingpong_prepare() {
   // the staged row kernels take up to kRowWarpsMax Stage<FORM> of dynamic shared memory;
   // set on the current device outside any stream capture (code creation)
-  for (auto f : {pp2_rows<1, false>, pp2_rows<1, true>}) {
+  for (auto f : {pp2_rows<1, false, false>, pp2_rows<1, true, false>, pp2_rows<1, false, true>, pp2_rows<1, true, true>}) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(sizeof(Stage<1>) * kRowWarpsMax));
     if (e != cudaSuccess) return e;
   }
-  for (auto f : {pp2_rows<0, false>, pp2_rows<0, true>}) {
+  for (auto f : {pp2_rows<0, false, false>, pp2_rows<0, true, false>, pp2_rows<0, false, true>, pp2_rows<0, true, true>}) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(sizeof(Stage<0>) * kRowWarpsMax));
     if (e != cudaSuccess) return e;
