@@ -58,3 +58,50 @@ def test_two_minima_random_checks():
         assert k1 >> 4 == sat[order[0]] and k2 >> 4 == sat[order[1]]
         if sat[order[0]] < qm:  # the position of the first minimum matters only then
             assert k1 & 15 == order[0]
+
+
+def _fma16(a, b, c):
+    """fma.rn on binary16: the exact a b + c (float64) rounded once."""
+    return np.asarray(np.asarray(a, np.float64) * np.float64(b) + np.asarray(c, np.float64)).astype(np.float16)
+
+
+def test_binary16_minima_decode_degree_le_8():
+    """The ping-pong row pass (checks of degree <= 8) decodes a key K = (16 m +
+    j) 2^-11, j <= 7, without leaving binary16: 1024 + 128 K rounds to 1024 + m
+    (j / 16 < 1/2), 2048 K + (17408 - 16 (1024 + m)) is 1024 + j, and the offset
+    rule max(1024 - beta + 128 K, 1024) is 1024 + max(m - beta, 0).  The minima
+    start at (16 Qm + 7) 2^-11, so that a saturated key keeps j = 7.  Every Qm,
+    m <= Qm, j <= 7 and offset beta <= 127."""
+    j = np.arange(8)
+    for qm in range(1, 128):
+        start = np.float16((16 * qm + 7) * S11)
+        assert float(start) == (16 * qm + 7) * S11
+        m = np.arange(qm + 1)[:, None]
+        K = ((16 * m + j) * S11).astype(np.float16)
+        assert np.all(K.astype(np.float64) * 2048 == 16 * m + j)  # every key is exact
+        assert np.all(K <= start)
+        M1 = _fma16(K, 128, 1024)
+        np.testing.assert_array_equal(M1.astype(np.int64), np.broadcast_to(1024 + m, K.shape))
+        n16 = _fma16(M1, -16, 17408)
+        np.testing.assert_array_equal(n16.astype(np.int64), np.broadcast_to(1024 - 16 * m, K.shape))
+        Ip = _fma16(K, 2048, n16)
+        np.testing.assert_array_equal(Ip.astype(np.int64), np.broadcast_to(1024 + j, K.shape))
+        for beta in range(128):
+            Ap = np.maximum(_fma16(K, 128, np.float16(1024 - beta)).astype(np.float64), 1024.0)
+            np.testing.assert_array_equal(Ap, np.broadcast_to(1024 + np.maximum(m - beta, 0), K.shape))
+        # the saturated start decodes to magnitude Qm
+        assert int(_fma16(start, 128, 1024)) == 1024 + qm
+
+
+def test_packed_normalized_halves():
+    """The normalized rule floor(m num / 2^shift) on the integer halves of a
+    pattern pair: ((m_lo | m_hi << 16) num mod 2^32) >> shift holds g(m_lo) in
+    byte 0 and g(m_hi) in byte 2, for m <= 127 and every num <= 2^shift,
+    shift <= 8 (no carry crosses the halves: m num < 2^16)."""
+    m = np.arange(128, dtype=np.uint64)
+    lo, hi = np.meshgrid(m, m, indexing="ij")
+    for shift in range(9):
+        for num in range(1, (1 << shift) + 1):
+            w = (((lo | (hi << np.uint64(16))) * np.uint64(num)) & np.uint64(0xFFFFFFFF)) >> np.uint64(shift)
+            np.testing.assert_array_equal(w & np.uint64(0xFF), (lo * np.uint64(num)) >> np.uint64(shift))
+            np.testing.assert_array_equal((w >> np.uint64(16)) & np.uint64(0xFF), (hi * np.uint64(num)) >> np.uint64(shift))
