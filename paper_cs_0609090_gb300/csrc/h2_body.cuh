@@ -78,14 +78,41 @@ __device__ __forceinline__ uint32_t hab(uint32_t a) {
 // num, shift), which floors the normalized magnitude like the integer rule.
 struct H2Rule {
   int32_t beta, num, shift;
+  uint32_t cb;  // binary16 pair of 1025 - beta
+  uint32_t c2;  // -0x64016401 num (mod 2^32)
   __device__ __forceinline__ int32_t g(int32_t x) const { return max((x - beta) * num, 0) >> shift; }
+  // The same rule on a minimum's key K = (16 m + j - 7) 2^-11 (0 <= j <= 14),
+  // without leaving binary16 for the offset: 1025 - beta + 128 K rounds to the
+  // integer 1025 + m - beta (|j - 7| / 16 < 1/2; every value from 1024.5 on
+  // has an exact integer grid), and the max with 1025 is 1025 + max(m - beta,
+  // 0).  The scaling then acts on the integer halves of that pattern (0x6401 +
+  // the value): pattern num - 0x64016401 num = value num per half (< 2^16, so
+  // no carry crosses), shifted; bytes 0 and 2 hold g < 256.  Returns the
+  // binary16 pair 1024 + g(m).
+  __device__ __forceinline__ uint32_t pat(uint32_t K) const {
+    const uint32_t a = hmax(hfma(K, h2c(128), cb), h2c(1025));
+    return __byte_perm((a * (uint32_t)num + c2) >> shift, 0x64u, 0x4240);
+  }
 };
-__host__ __device__ inline H2Rule make_h2rule(const IntRule& r) {
+// beta, num, shift as H2Rule::g takes them (plain: 0, 1, 0; offset: beta, 1,
+// 0; normalized: 0, num, shift), with beta <= 127.
+__host__ __device__ inline H2Rule h2rule(int32_t beta, int32_t num, int32_t shift) {
   H2Rule h;
-  h.beta = r.rule == 1 ? r.beta : 0;
-  h.num = r.rule == 2 ? r.num : 1;
-  h.shift = r.rule == 2 ? r.shift : 0;
+  h.beta = beta;
+  h.num = num;
+  h.shift = shift;
+  h.cb = hbits(1025 - beta) * 0x10001u;
+  h.c2 = 0u - 0x64016401u * (uint32_t)num;
   return h;
+}
+__host__ __device__ inline H2Rule make_h2rule(const IntRule& r) {
+  return h2rule(r.rule == 1 ? r.beta : 0, r.rule == 2 ? r.num : 1, r.rule == 2 ? r.shift : 0);
+}
+
+// (j - 7) 2^-11 as a binary16 pair: the position term of the keys of checks of
+// degree <= 15.
+__host__ __device__ constexpr uint32_t key_pos15(int j) {
+  return j >= 7 ? h2c_q11(j - 7) : (h2c_q11(7 - j) | 0x80008000u);
 }
 
 // Decision parity of check m for the G frames (bit g set: unsatisfied).
@@ -139,8 +166,18 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
                                                uint4* __restrict__ St, uint16_t* __restrict__ Lm) {
   constexpr int P = G / 2;
   constexpr int NJ = D > 0 ? D : DMAX;
-  // (16 Qm + 15) 2^-11: the largest key of a magnitude saturated to Qm
-  const uint32_t ksat = hfma(qm2, h2c_q11(16), h2c_q11(15));
+  // Checks of degree <= 8 (KH): keys (16 |u| + j - 7) 2^-11 and the minima
+  // decoded in binary16 (H2Rule::pat); wider checks: keys (16 |u| + j) 2^-11
+  // clamped to 1, decoded through integers.  The minima start at the key of a
+  // magnitude saturated to Qm at the last position the key form holds:
+  // (16 Qm + 7) 2^-11 or (16 Qm + 15) 2^-11.  (The binary16 decode holds up
+  // to degree 15, but on the N=7493 code's checks of degree 14 and 15 the
+  // frame-resident kernel ran 3 % slower with it: 2.89 against 2.80 ms.)
+  constexpr bool KH = NJ <= 8;
+  const uint32_t ksat = hfma(qm2, h2c_q11(16), h2c_q11(KH ? 7 : 15));
+  // position constants of the stored n~: the pattern 1024 + n~ (8-byte state
+  // under KH) or the value n~
+  constexpr int IB = (KH && C8) ? 1024 : 0;
   // one frame pair: the pass-1 handles stay in registers for pass 2; two pairs
   // need those registers for state and reload them
   constexpr bool KEEP = (P == 1 && FORM == 1 && !ES && ACC != 2);
@@ -155,7 +192,8 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
         const uint2 s = reinterpret_cast<const uint2*>(St)[ad.st(m) + p];
         A2[p] = hsub(__byte_perm(s.x, 0x64u, 0x4140), 0x64006400u);
         B2[p] = hsub(__byte_perm(s.x, 0x64u, 0x4342), 0x64006400u);
-        I2[p] = hsub(__byte_perm(s.y, 0x64u, 0x4240), 0x64006400u);
+        I2[p] = __byte_perm(s.y, 0x64u, 0x4240);
+        if constexpr (IB == 0) I2[p] = hsub(I2[p], 0x64006400u);
         S[p] = s.y;
       } else {
         const uint4 s = St[ad.st(m) + p];
@@ -197,7 +235,7 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
         if constexpr (FORM == 1) {
           // f(A, B, n, n~) = A + (B - A) [j = n~] (exact: small integers), and the
           // stored sign s_mn on the binary16 sign bit
-          L = hfma(D2[p], heq_one(I2[p], h2c(j)), A2[p]) ^ (SR[p] & 0x80008000u);
+          L = hfma(D2[p], heq_one(I2[p], h2c(IB + j)), A2[p]) ^ (SR[p] & 0x80008000u);
           SR[p] += SR[p];
         } else {
           // byte L + 128 -> binary16 128 + (L + 128)/8 -> 8 h - 1152 = L
@@ -214,8 +252,10 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
         // exact for |u| <= 127 (16 |u| + j < 2048 fits 11 significand bits).
         // Keys of |u| > Qm (Qm <= 127) exceed the minima's start (16 Qm + 15)
         // 2^-11, so the minima come out as 16 min(|u|, Qm) + j; where both
-        // are saturated A = B and the position of the first does not matter
-        const uint32_t key = hfma_sat(hab(u), h2c_q11(16), h2c_q11(j));
+        // are saturated A = B and the position of the first does not matter.
+        // KH: (16 |u| + j - 7) 2^-11, exact for |u| <= 127 and above the
+        // start (16 Qm + 7) 2^-11 for every |u| > Qm (no clamp needed)
+        const uint32_t key = KH ? hfma(hab(u), h2c_q11(16), key_pos15(j)) : hfma_sat(hab(u), h2c_q11(16), h2c_q11(j));
         // at j = 0 the second minimum stays the start value: every key is at
         // most 1, so min(ksat, max(ksat, key)) = ksat
         if (j != 0) K2[p] = hmin(K2[p], hmax(K1[p], key));
@@ -235,18 +275,33 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
     const uint32_t pm = ((__popc(NEG[p] & 0xffffu) & 1) ? 0x0000ffffu : 0u) |
                         ((__popc(NEG[p] >> 16) & 1) ? 0xffff0000u : 0u);
     Sn[p] = (NEG[p] ^ pm) & (dlane | (dlane << 16));
-    // keys back to 16 min(|u|, Qm) + j (exact: a power of two)
-    const uint32_t k1 = hfma(K1[p], h2c(2048), 0u), k2 = hfma(K2[p], h2c(2048), 0u);
-    const int32_t k1l = h_lo_int(k1), k1h = h_hi_int(k1);
-    const int32_t k2l = h_lo_int(k2), k2h = h_hi_int(k2);
-    const int32_t al = rule.g(k1l >> 4), ah = rule.g(k1h >> 4);
-    const int32_t bl = rule.g(k2l >> 4), bh = rule.g(k2h >> 4);
-    An[p] = small_to_h2(al, ah);
-    Bn[p] = small_to_h2(bl, bh);
-    In[p] = small_to_h2(k1l & 15, k1h & 15);
-    if constexpr (C8) {
-      W0[p] = (uint32_t)al | ((uint32_t)ah << 8) | ((uint32_t)bl << 16) | ((uint32_t)bh << 24);
-      W1[p] = (uint32_t)(k1l & 15) | ((uint32_t)(k1h & 15) << 16) | (Sn[p] & 0xff00ff00u);
+    if constexpr (KH) {
+      // 1025 + m1 (the rounding of H2Rule::pat with beta = 0), then
+      // 2048 K1 + (17424 - 16 (1025 + m1)) = 16 m1 + n~ - 7 + 1024 - 16 m1:
+      // In holds the pattern 1017 + n~ (exact: the integers from 512 on)
+      const uint32_t M1 = hfma(K1[p], h2c(128), h2c(1025));
+      In[p] = hfma(K1[p], h2c(2048), hfma(M1, h2c(16) | 0x80008000u, h2c(17424)));
+      const uint32_t Ap = rule.pat(K1[p]), Bp = rule.pat(K2[p]);  // 1024 + g(m)
+      An[p] = hsub(Ap, 0x64006400u);
+      Bn[p] = hsub(Bp, 0x64006400u);
+      if constexpr (C8) {
+        W0[p] = __byte_perm(Ap, Bp, 0x6420);
+        W1[p] = (hadd(In[p], h2c(7)) & 0x00ff00ffu) | (Sn[p] & 0xff00ff00u);
+      }
+    } else {
+      // keys back to 16 min(|u|, Qm) + j (exact: a power of two)
+      const uint32_t k1 = hfma(K1[p], h2c(2048), 0u), k2 = hfma(K2[p], h2c(2048), 0u);
+      const int32_t k1l = h_lo_int(k1), k1h = h_hi_int(k1);
+      const int32_t k2l = h_lo_int(k2), k2h = h_hi_int(k2);
+      const int32_t al = rule.g(k1l >> 4), ah = rule.g(k1h >> 4);
+      const int32_t bl = rule.g(k2l >> 4), bh = rule.g(k2h >> 4);
+      An[p] = small_to_h2(al, ah);
+      Bn[p] = small_to_h2(bl, bh);
+      In[p] = small_to_h2(k1l & 15, k1h & 15);
+      if constexpr (C8) {
+        W0[p] = (uint32_t)al | ((uint32_t)ah << 8) | ((uint32_t)bl << 16) | ((uint32_t)bh << 24);
+        W1[p] = (uint32_t)(k1l & 15) | ((uint32_t)(k1h & 15) << 16) | (Sn[p] & 0xff00ff00u);
+      }
     }
     if constexpr (ES) par |= ((Y[p] >> 15) & 1u) << (2 * p) | ((Y[p] >> 31) & 1u) << (2 * p + 1);
   }
@@ -272,14 +327,14 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
       }
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const uint32_t L = hfma(Dn[p], heq_one(In[p], h2c(j)), An[p]) ^ (SN[p] & 0x80008000u);
+        const uint32_t L = hfma(Dn[p], heq_one(In[p], h2c(KH ? 1017 + j : j)), An[p]) ^ (SN[p] & 0x80008000u);
         SN[p] += SN[p];
         int32_t v = (int32_t)hadd(L, h2c(1536));
         uint32_t Lo = 0;
         if constexpr (ACC != 0) {
           // the previous message of this position, as in pass 1
           if constexpr (FORM == 1) {
-            Lo = hfma(D2[p], heq_one(I2[p], h2c(j)), A2[p]) ^ (SO[p] & 0x80008000u);
+            Lo = hfma(D2[p], heq_one(I2[p], h2c(IB + j)), A2[p]) ^ (SO[p] & 0x80008000u);
             SO[p] += SO[p];
           } else {
             const uint32_t b = (P == 1) ? lold : (lold >> (16 * p));
@@ -306,7 +361,7 @@ __device__ __forceinline__ uint32_t check_body(const Addr& ad, const uint16_t* _
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       if constexpr (C8) reinterpret_cast<uint2*>(St)[ad.st(m) + p] = make_uint2(W0[p], W1[p]);
-      else St[ad.st(m) + p] = make_uint4(An[p], Bn[p], In[p], Sn[p]);
+      else St[ad.st(m) + p] = make_uint4(An[p], Bn[p], KH ? hsub(In[p], h2c(1017)) : In[p], Sn[p]);
     }
   }
   return par;

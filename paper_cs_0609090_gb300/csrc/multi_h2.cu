@@ -126,7 +126,7 @@ __device__ void decode_pair(const MultiJob& jb, int pair, unsigned char* smem, M
   const int nv = CL ? max(0, min(N - v0, jb.ns)) : N;
   const int rows = CL ? __ldg(jb.rows + rank) : jb.M;
   const uint8_t* __restrict__ rdeg = jb.rdeg + (CL ? (size_t)rank * jb.mr : 0);
-  const H2Rule hr{jb.beta, jb.num, jb.shift};
+  const H2Rule hr = h2rule(jb.beta, jb.num, jb.shift);
   const uint32_t qm2 = ints_to_h2(jb.qm, jb.qm);
   const int slot = CL ? 0 : s;
   const bool es = ES && jb.early_stop != 0;

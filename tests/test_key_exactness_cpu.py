@@ -105,3 +105,50 @@ def test_packed_normalized_halves():
             w = (((lo | (hi << np.uint64(16))) * np.uint64(num)) & np.uint64(0xFFFFFFFF)) >> np.uint64(shift)
             np.testing.assert_array_equal(w & np.uint64(0xFF), (lo * np.uint64(num)) >> np.uint64(shift))
             np.testing.assert_array_equal((w >> np.uint64(16)) & np.uint64(0xFF), (hi * np.uint64(num)) >> np.uint64(shift))
+
+
+def _pattern_pair(lo, hi):
+    """32-bit word of two binary16 values (lo in bits 0-15)."""
+    return (np.asarray(lo, np.float16).view(np.uint16).astype(np.uint64)
+            | (np.asarray(hi, np.float16).view(np.uint16).astype(np.uint64) << np.uint64(16)))
+
+
+def test_binary16_decode_shared_check_body():
+    """The shared check body's binary16 decode (checks of degree <= 8 there; the
+    form holds to degree 15): keys (16 |u| + j - 7) 2^-11 without a clamp, the
+    minima started at (16 Qm + 7) 2^-11.  Every key of |u| <= 127 is exact,
+    every |u| > Qm keys above the start (|u| up to 2300, rounded or not), and
+    the decode gives 1025 + m (fma(K, 128, 1025)), 1017 + j (fma(K, 2048,
+    fma(1025 + m, -16, 17424))) and the rule's pattern 1024 + g(m):
+    max(fma(K, 128, 1025 - beta), 1025), then (pattern num - 0x64016401 num)
+    >> shift on the 32-bit pair, bytes 0 and 2 behind 0x64."""
+    j = np.arange(15)
+    u_all = np.arange(2301)
+    for qm in range(1, 128):
+        start = np.float16((16 * qm + 7) * S11)
+        keys = _fma16(u_all[:, None], S7, (j - 7) * S11)
+        exact = (16 * u_all[:, None] + j - 7) * S11
+        assert np.all(keys[:128].astype(np.float64) == exact[:128])
+        assert np.all(keys[qm + 1:] > start)
+        m = np.arange(qm + 1)[:, None]
+        K = keys[:qm + 1]
+        M1 = _fma16(K, 128, 1025)
+        np.testing.assert_array_equal(M1.astype(np.int64), np.broadcast_to(1025 + m, K.shape))
+        In = _fma16(K, 2048, _fma16(M1, -16, 17424))
+        np.testing.assert_array_equal(In.astype(np.int64), np.broadcast_to(1017 + j, K.shape))
+        for beta in (0, 1, 2, 5, 127):
+            a = np.maximum(_fma16(K, 128, np.float16(1025 - beta)).astype(np.float64), 1025.0)
+            np.testing.assert_array_equal(a, np.broadcast_to(1025 + np.maximum(m - beta, 0), K.shape))
+        assert int(_fma16(start, 128, 1025)) == 1025 + qm
+    # the integer step on pattern pairs 1025 + v (v <= 127) for the normalized rule
+    v = np.arange(128)
+    lo, hi = np.meshgrid(v, v, indexing="ij")
+    w = _pattern_pair(1025.0 + lo, 1025.0 + hi)
+    for shift in range(9):
+        for num in sorted({1, 2, 3, (1 << shift) - 1, 1 << shift} - {0}):
+            if num > (1 << shift):
+                continue
+            c2 = (-0x64016401 * num) % (1 << 32)
+            x = ((w * np.uint64(num) + np.uint64(c2)) % np.uint64(1 << 32)) >> np.uint64(shift)
+            np.testing.assert_array_equal(x & np.uint64(0xFF), (lo * num) >> shift)
+            np.testing.assert_array_equal((x >> np.uint64(16)) & np.uint64(0xFF), (hi * num) >> shift)
