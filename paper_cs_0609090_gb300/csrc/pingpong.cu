@@ -72,6 +72,9 @@ constexpr uint32_t kFull = 0xffffffffu;
 #ifndef LDPC_PP2_UNROLL
 #define LDPC_PP2_UNROLL 4
 #endif
+#ifndef LDPC_PP2_ALT_ORDER
+#define LDPC_PP2_ALT_ORDER 1
+#endif
 
 constexpr int kWarps = 8;   // per block (pp2_final; the row kernel's default)
 constexpr int kRowWarpsMax = 16;  // the row kernel takes 4, 8 or 16 warps per block
@@ -91,6 +94,15 @@ constexpr bool kShiftFma = LDPC_PP2_SHIFT_FMA != 0;
 constexpr bool kEqFma = LDPC_PP2_EQ_FMA != 0;
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Chunk (64 pairs) of a row or syndrome launch for iteration k.  Blocks start in
+// chunk-major order (blockIdx.y is the slow index), and successive iterations
+// take the chunks in opposite orders, so that each iteration starts on the
+// chunks whose posterior lines and states the previous one touched last and
+// left in L2.
+__device__ __forceinline__ int chunk_of(int k) {
+  return (LDPC_PP2_ALT_ORDER && (k & 1)) ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+}
 
 struct PP2 {
   uint32_t* zb;    // [2][N][FP]
@@ -433,7 +445,7 @@ template <int FORM, bool ES, bool NORM>
 __global__ void __launch_bounds__(kRowWarpsMax * 32) __maxnreg__(FORM == 1 ? kRegs1 : kRegs0)
 pp2_rows(const DevCode c, const IntRule ir, PP2 s, int k) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.y * 64 + 2 * lane;
+  const int p = chunk_of(k) * 64 + 2 * lane;
   const int FP = s.FP;
   uint32_t aA = valid_bits(p, s.F), aB = valid_bits(p + 1, s.F);
   if (ES) {
@@ -572,7 +584,7 @@ __global__ void __launch_bounds__(256) pp2_init(const DevCode c, const int8_t* _
 template <bool ES>
 __global__ void __launch_bounds__(kWarps * 32) pp2_final(const DevCode c, PP2 s, int K) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.y * 64 + 2 * lane;
+  const int p = chunk_of(K + 1) * 64 + 2 * lane;
   const int FP = s.FP;
   uint32_t aA = valid_bits(p, s.F), aB = valid_bits(p + 1, s.F);
   if (ES) {
