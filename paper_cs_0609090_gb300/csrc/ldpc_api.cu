@@ -250,7 +250,7 @@ ldpc_status choose(const ldpc_code* c, const ldpc_decode_params* p, int32_t n_fr
       return LDPC_OK;
     }
     return fail(LDPC_ERR_UNSUPPORTED, "code (N=%d, M=%d, E=%d, row degree <= %d, column degree <= %d) "
-                "cannot run on the requested frame-resident kernel (%d)",
+                "cannot run on the requested kernel (%d)",
                 c->N, c->M, c->E, c->max_row_deg, c->max_col_deg, p->kernel);
   }
   if (p->dtype == LDPC_DTYPE_INT8 && (p->form == LDPC_FORM_TWO_SCAN || p->form == LDPC_FORM_TWO_SCAN_1BIT)) {

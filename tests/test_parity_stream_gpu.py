@@ -244,3 +244,43 @@ def test_stream_workspace_contract(L):
     assert e.value.status == L.LDPC_ERR_INVALID_ARG
     L.ldpc_decode_batch(h.handle, params, q, 2, bits, it, ok, None, P(base), need)
     torch.cuda.synchronize()
+
+
+def _mixed_rows(n_vars, n_checks, dmin, dmax, seed):
+    """Rows of degrees dmin..dmax on random distinct variables, every variable
+    in at least one check, ordered so that warps of four checks mix degrees."""
+    rng = np.random.default_rng(seed)
+    rows = [sorted(rng.choice(n_vars, size=int(rng.integers(dmin, dmax + 1)), replace=False).tolist())
+            for _ in range(n_checks)]
+    seen = {v for r in rows for v in r}
+    for v in range(n_vars):
+        if v not in seen:
+            r = rows[int(rng.integers(n_checks))]
+            if len(r) < dmax:
+                r.append(v)
+                r.sort()
+            else:
+                rows.append([v, (v + 1) % n_vars])
+    return rows
+
+
+@pytest.mark.parametrize("dmax", [7, 8])
+@pytest.mark.parametrize("form", FORMS_INT)
+def test_pingpong_mixed_degrees(L, form, dmax):
+    """The ping-pong decoder on codes of row degrees 2 to 7 or 8: mixed degrees
+    in a warp's checks and uniform degrees other than 6 and 7 (the unstaged
+    path) and uniform runs of 6 and 7 (the staged path), against the oracle
+    under every rule, with and without early stop, with a small Qm (both minima
+    saturated) and the largest, on random LLRs."""
+    rows = _mixed_rows(640, 300, 2, dmax, seed=11 + dmax)
+    r = np.random.default_rng(5)
+    rows += [sorted(r.choice(640, size=d, replace=False).tolist()) for d in [6] * 64 + [dmax] * 64]
+    code = I.from_rows(640, rows)
+    assert int(np.max(np.diff(code.row_ptr))) == dmax
+    assert int(np.max(np.bincount(code.col_idx))) <= 14  # 128 + 15 Qm <= 2048 for every Qm below
+    rng = np.random.default_rng(dmax)
+    q0 = rng.integers(-20, 21, size=(131, 640)).astype(np.int8)
+    for p in (dict(rule="offset", offset=1, msg_sat=127), dict(rule="normalized", norm_num=3, norm_shift=2, msg_sat=5),
+              dict(rule="plain", msg_sat=3), dict(rule="normalized", norm_num=7, norm_shift=3, msg_sat=127)):
+        for es in (0, 1):
+            _int(L, code, q0, form, dict(p, max_iter=12, early_stop=es), kernel="pingpong")
