@@ -439,7 +439,7 @@ typedef struct {
  *                 streams.  The autotuner keeps a schedule fixed by 1 or 2.
  *   stream_warps  warps per CTA of the ping-pong decoder's row kernel for the
  *                 streamed codes (four checks per warp, so 16, 32 or 64 checks
- *                 per CTA): 4, 8 or 16; 0 (default) 8 until ldpc_multi_autotune
+ *                 per CTA): 4, 8 or 16; 0 (default) 4 until ldpc_multi_autotune
  *                 times the three; a value set here is kept by the autotuner. */
 typedef struct {
   int32_t threads;

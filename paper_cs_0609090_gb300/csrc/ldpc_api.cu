@@ -610,9 +610,10 @@ ldpc_status ldpc_decode_batch(const ldpc_code* code, const ldpc_decode_params* p
                                       static_cast<const int8_t*>(llr), n_frames, params->max_iter, params->early_stop,
                                       hard_bits, iters_used, syndrome_ok, static_cast<int16_t*>(llr_out), st);
   } else if (ch.kind == Choice::PINGPONG_INT8) {
+    // row kernel blocks of 4 warps (N=64800, 1024 frames: 7.04 ms against 7.13 at 8 warps, same box)
     err = ldpc::pingpong_int8_decode(v, r, form, ch.pingpong, workspace, static_cast<const int8_t*>(llr), n_frames,
                                      params->max_iter, params->early_stop, hard_bits, iters_used, syndrome_ok,
-                                     static_cast<int16_t*>(llr_out), st);
+                                     static_cast<int16_t*>(llr_out), st, 4);
   } else if (ch.kind == Choice::PERSIST_INT8) {
     err = ldpc::persist_int8_decode(v, r, form, ch.persist, workspace, code->sm_count,
                                     static_cast<const int8_t*>(llr), n_frames, params->max_iter, params->early_stop,

@@ -415,7 +415,7 @@ cudaError_t launch_plan(const ldpc_multi* p, void* ws, cudaStream_t st) {
       e = ldpc::pingpong_int8_decode(view(jb.code), r, p->form, sj.pp, static_cast<char*>(ws) + sj.offset, jb.llr,
                                      jb.n_frames, jb.params.max_iter, jb.params.early_stop, jb.hard_bits,
                                      jb.iters_used, jb.syndrome_ok, jb.llr_out, ss,
-                                     p->shape.stream_warps ? p->shape.stream_warps : 8);
+                                     p->shape.stream_warps ? p->shape.stream_warps : 4);
     else
       e = ldpc::stream_int8_decode(view(jb.code), r, p->form, sj.layout, static_cast<char*>(ws) + sj.offset,
                                    jb.code->sm_count, jb.llr, jb.n_frames, jb.params.max_iter, jb.params.early_stop,

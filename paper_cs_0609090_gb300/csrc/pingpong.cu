@@ -76,7 +76,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 #define LDPC_PP2_ALT_ORDER 1
 #endif
 
-constexpr int kWarps = 8;   // per block (pp2_final; the row kernel's default)
+constexpr int kWarps = 8;   // per block of pp2_final (the row kernel takes its block size from the caller)
 constexpr int kRowWarpsMax = 16;  // the row kernel takes 4, 8 or 16 warps per block
 // registers per thread of the row kernel: those of MINB CTAs of 256 threads per
 // SM, rounded down to the allocation unit of 8
